@@ -1,0 +1,198 @@
+/*
+ * flycoo.h -- C ABI of the GB300 (sm_103a) FLYCOO spMTTKRP library.
+ *
+ * The library computes sparse MTTKRP (spMTTKRP) for every mode of an N-mode
+ * sparse tensor held in the FLYCOO format, and remaps the tensor to the next
+ * mode's shard order inside the same pass (Wijeratne, Kannan, Prasanna,
+ * "Dynasor", arXiv 2309.09131: Section II-B, Section III, Algorithm 2).
+ *
+ * Conventions for every entry point:
+ *  - Pointers named d_* are DEVICE pointers on the handle's device; pointers
+ *    named h_* are HOST pointers.  The caller owns every buffer it passes;
+ *    the handle owns the FLYCOO buffers it allocates in flycoo_create and
+ *    frees them in flycoo_destroy.
+ *  - Dense matrices are row-major.  Factor matrix Y_w is I_w x R; an output
+ *    M_n is I_n x R in FP32.  Coordinates are 0-based (Section II-A).
+ *  - Work is ordered on the given stream (a cudaStream_t; NULL is the legacy
+ *    default stream).  Only flycoo_create, the export_* calls that fill host
+ *    buffers, flycoo_cp_als_step (its scalar fit) and flycoo_timing_read wait
+ *    for the stream.
+ *  - Every entry point returns a flycoo_status and never aborts or traps;
+ *    flycoo_last_error() then describes the failure (per calling thread).
+ *  - A handle is not thread-safe: calls on one handle must not overlap.
+ */
+#ifndef FLYCOO_H
+#define FLYCOO_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+struct CUstream_st;
+typedef struct CUstream_st *flycoo_stream_t; /* a cudaStream_t */
+
+typedef enum {
+    FLYCOO_OK = 0,
+    FLYCOO_ERR_INVALID_ARG = 1,  /* a size, mode, pointer or parameter is invalid   */
+    FLYCOO_ERR_INDEX_RANGE = 2,  /* a coordinate is >= its mode's size               */
+    FLYCOO_ERR_OOM = 3,          /* a device or host allocation failed               */
+    FLYCOO_ERR_LAYOUT = 4,       /* the tensor is not in the layout the call needs   */
+    FLYCOO_ERR_NOT_SPD = 5,      /* an ALS normal-equation matrix is not SPD         */
+    FLYCOO_ERR_TIMEOUT = 6,      /* a bounded device wait gave up                    */
+    FLYCOO_ERR_CUDA = 7,         /* a CUDA runtime call failed                       */
+    FLYCOO_ERR_UNSUPPORTED = 8   /* valid, but not built (mode count, rank, dtype)   */
+} flycoo_status;
+
+typedef enum {
+    FLYCOO_F32 = 0,  /* factor matrices stored as IEEE binary32                      */
+    FLYCOO_BF16 = 1  /* factor matrices stored as bfloat16; products and sums in FP32 */
+} flycoo_dtype;
+
+#define FLYCOO_MAX_MODES 8
+
+/* Partitioning parameters (Section III-A and III-C).  Zero selects the default.
+ *  m[n]  super-shard width of mode n: super-shard j holds the nonzeros whose
+ *        mode-n index lies in [j*m[n], (j+1)*m[n]).  Default ceil(I_n / bins)
+ *        (Eq. 1 with q = 1), so there are about `bins` super-shards per mode.
+ *  g     shard size in nonzeros: each super-shard is cut into runs of g
+ *        consecutive nonzeros (the last one shorter).  Default 8192, lowered
+ *        to keep >= 4 shards per bin on small tensors (never below 256).
+ *  bins  number of schedule bins of Algorithm 3, which is also the number of
+ *        thread blocks of the fused kernel.  Default: 4 x the SM count. */
+typedef struct {
+    uint64_t m[FLYCOO_MAX_MODES];
+    uint64_t g;
+    uint32_t bins;
+    uint32_t reserved;
+} flycoo_params;
+
+/* Read-only description of a handle. */
+typedef struct {
+    int32_t N;                                  /* number of modes                    */
+    int32_t layout_mode;                        /* mode whose layout L_n is current   */
+    uint64_t nnz;                               /* nonzeros (duplicates count apart)  */
+    uint64_t dims[FLYCOO_MAX_MODES];            /* I_n                                */
+    uint64_t m[FLYCOO_MAX_MODES];               /* super-shard width used             */
+    uint64_t g;                                 /* shard size used                    */
+    uint32_t bins;                              /* schedule bins used                 */
+    uint32_t elem_bytes;                        /* bytes of one stored nonzero        */
+    uint64_t super_shards[FLYCOO_MAX_MODES];    /* k_n = ceil(I_n / m_n)              */
+    uint64_t shards[FLYCOO_MAX_MODES];          /* S_n = sum_j ceil(|SS_n,j| / g)     */
+    uint64_t boundary_rows[FLYCOO_MAX_MODES];   /* rows that a shard starts or ends in */
+    uint64_t device_bytes;                      /* device memory the handle holds     */
+} flycoo_info;
+
+typedef struct flycoo_tensor *flycoo_handle;
+
+/* ------------------------------------------------------------------------ */
+/* flycoo_create -- convert a COO tensor to FLYCOO (Section III-A; the       */
+/* preprocessing of Section V-J).  For every mode n it computes the layout   */
+/* L_n (nonzeros ordered by (c_n, c_{n-1}, ..., c_{n+1}, input position)),   */
+/* the super-shard and shard pointers, each nonzero's slot in L_{(n+1) mod N} */
+/* and the Algorithm 3 schedules, then stores the tensor in layout L_0.      */
+/*  N       number of modes, 3 <= N <= 5.                                    */
+/*  h_dims  N mode sizes, each in [1, 2^32 - 1].                             */
+/*  nnz     nonzeros, < 2^32 - 1.  0 is allowed.                             */
+/*  d_idx   N x nnz uint32, mode-major: coordinate of mode w of nonzero e is */
+/*          d_idx[w*nnz + e].  Copied; the caller may free it on return.      */
+/*  d_vals  nnz float32 values.  Copied.                                     */
+/*  params  NULL or partition parameters (zeros = defaults).                 */
+/*  out     receives the handle.                                             */
+/* Errors: INVALID_ARG, INDEX_RANGE (any coordinate >= its I_w), OOM, CUDA.  */
+/* Waits for `stream`.                                                       */
+/* ------------------------------------------------------------------------ */
+flycoo_status flycoo_create(int N, const uint64_t *h_dims, uint64_t nnz, const uint32_t *d_idx,
+                            const float *d_vals, const flycoo_params *params,
+                            flycoo_stream_t stream, flycoo_handle *out);
+
+/* Free every buffer the handle owns.  NULL is ignored. */
+void flycoo_destroy(flycoo_handle h);
+
+/* ------------------------------------------------------------------------ */
+/* flycoo_spmttkrp -- spMTTKRP of one mode with the fused dynamic remap      */
+/* (Algorithm 2 for one value of n; elementwise equation of Section IV):     */
+/*   d_out[i, r] = sum over nonzeros x with c_mode(x) = i of                 */
+/*                 val(x) * prod_{w != mode} Y_w[c_w(x), r]                   */
+/* Rows that no nonzero touches are written as 0.  Accumulation is FP32 in a */
+/* fixed order: the result is bitwise reproducible for a given handle.       */
+/*  mode       output mode; the tensor must be in layout L_mode.             */
+/*  h_factors  HOST array of N DEVICE pointers, Y_w is I_w x R row-major in  */
+/*             `fdt`, 16-byte aligned.  Entry `mode` is not read (may be     */
+/*             NULL).                                                        */
+/*  R          rank: 16, 32 or 64.                                           */
+/*  d_out      I_mode x R FP32, 16-byte aligned, written in full.  It must   */
+/*             not overlap a factor.                                         */
+/*  next_mode  -1: no remap.  (mode + 1) mod N: store every nonzero at its   */
+/*             slot of L_next during the pass (Algorithm 2, the Store of the  */
+/*             remap step); the tensor is then in layout L_next.             */
+/* Errors: INVALID_ARG, LAYOUT (tensor not in L_mode), UNSUPPORTED, CUDA.    */
+/* ------------------------------------------------------------------------ */
+flycoo_status flycoo_spmttkrp(flycoo_handle h, int mode, const void *const *h_factors,
+                              flycoo_dtype fdt, int R, float *d_out, int next_mode,
+                              flycoo_stream_t stream);
+
+/* ------------------------------------------------------------------------ */
+/* flycoo_remap -- dynamic tensor remapping alone (Section III-B): move the  */
+/* tensor from its current layout to L_next_mode.  Each step stores every    */
+/* nonzero at its slot of the following mode's layout; the call takes       */
+/* (next_mode - layout_mode) mod N steps (0 steps if already there).        */
+/* Errors: INVALID_ARG, CUDA.                                                */
+/* ------------------------------------------------------------------------ */
+flycoo_status flycoo_remap(flycoo_handle h, int next_mode, flycoo_stream_t stream);
+
+/* Fill *out with the handle's sizes and parameters. */
+flycoo_status flycoo_get_info(flycoo_handle h, flycoo_info *out);
+
+/* ------------------------------------------------------------------------ */
+/* Exports of the FLYCOO structures, for checks against a reference.         */
+/* ------------------------------------------------------------------------ */
+
+/* The current layout as COO: d_idx_out (N x nnz uint32, mode-major, input  */
+/* coordinate order) and d_vals_out (nnz float32), position p of the layout */
+/* in column p.  Stream-ordered. */
+flycoo_status flycoo_export_layout(flycoo_handle h, uint32_t *d_idx_out, float *d_vals_out,
+                                   flycoo_stream_t stream);
+
+/* Section III-A pointers of mode n into host buffers (any may be NULL):     */
+/*  h_ss_ptr[k_n + 1]  start of super-shard j in L_n, then nnz;              */
+/*  h_shard_ptr[S_n+1] start of each shard in L_n, then nnz;                 */
+/*  h_first_row[S_n], h_last_row[S_n]  mode-n index of the first and last   */
+/*  nonzero of each shard.                                                   */
+flycoo_status flycoo_export_partition(flycoo_handle h, int mode, uint64_t *h_ss_ptr,
+                                      uint64_t *h_shard_ptr, uint32_t *h_first_row,
+                                      uint32_t *h_last_row);
+
+/* Algorithm 3 schedules of mode n as CSR lists into host buffers:           */
+/*  which = 0: super-shards binned by shard count (the SS_List of the paper),*/
+/*             h_items has k_n entries;                                      */
+/*  which = 1: shards binned by nonzero count (the thread-block schedule of */
+/*             the fused kernel), h_items has S_n entries.                   */
+/* Bin b holds h_items[h_bin_ptr[b] .. h_bin_ptr[b+1]) in assignment order;  */
+/* h_bin_ptr has bins + 1 entries.                                           */
+flycoo_status flycoo_export_schedule(flycoo_handle h, int mode, int which, uint64_t *h_bin_ptr,
+                                     uint64_t *h_items);
+
+/* d_next[p] (nnz uint32): slot in L_{(mode+1) mod N} of the nonzero at      */
+/* position p of L_mode -- the remap permutation of mode `mode`.             */
+flycoo_status flycoo_export_next(flycoo_handle h, int mode, uint32_t *d_next,
+                                 flycoo_stream_t stream);
+
+/* ------------------------------------------------------------------------ */
+/* Kernel timing of the fused spMTTKRP + remap kernel.  While enabled, each  */
+/* flycoo_spmttkrp records CUDA events around that kernel on its stream.     */
+/* flycoo_timing_read waits for them, returns the summed milliseconds and   */
+/* the launch count since the last read, and clears them.                    */
+/* ------------------------------------------------------------------------ */
+flycoo_status flycoo_timing_enable(flycoo_handle h, int enable);
+flycoo_status flycoo_timing_read(flycoo_handle h, double *h_ms, uint64_t *h_launches);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *flycoo_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FLYCOO_H */

@@ -1,0 +1,25 @@
+"""GB300-native (sm_103a) FLYCOO spMTTKRP with dynamic tensor remapping.
+
+The computation lives in the CUDA library ``_lib/libflycoo.so`` (C ABI in
+``include/flycoo.h``); this package is its ctypes binding plus a thin owning
+wrapper.  PyTorch supplies device memory and streams only.
+"""
+from ._native import (  # noqa: F401
+    BF16,
+    F32,
+    FlycooError,
+    flycoo_create,
+    flycoo_destroy,
+    flycoo_export_layout,
+    flycoo_export_next,
+    flycoo_export_partition,
+    flycoo_export_schedule,
+    flycoo_get_info,
+    flycoo_last_error,
+    flycoo_remap,
+    flycoo_spmttkrp,
+    flycoo_timing_enable,
+    flycoo_timing_read,
+    make_params,
+)
+from .flycoo import FlycooTensor  # noqa: F401

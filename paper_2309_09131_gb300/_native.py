@@ -1,0 +1,236 @@
+"""ctypes binding of ``include/flycoo.h``: one Python function per C entry
+point, same name, argument marshalling only (torch tensors -> device
+pointers, the current torch stream -> cudaStream_t).  Every computation runs
+in the CUDA library; there is no fallback.  A missing library raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import List, Optional, Sequence
+
+import numpy as np
+import torch  # loads the CUDA runtime the library shares
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "libflycoo.so")
+MAX_MODES = 8
+
+OK = 0
+STATUS_NAMES = {
+    0: "FLYCOO_OK", 1: "FLYCOO_ERR_INVALID_ARG", 2: "FLYCOO_ERR_INDEX_RANGE", 3: "FLYCOO_ERR_OOM",
+    4: "FLYCOO_ERR_LAYOUT", 5: "FLYCOO_ERR_NOT_SPD", 6: "FLYCOO_ERR_TIMEOUT", 7: "FLYCOO_ERR_CUDA",
+    8: "FLYCOO_ERR_UNSUPPORTED",
+}
+F32 = 0
+BF16 = 1
+
+
+class FlycooError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        self.status = status
+        self.status_name = STATUS_NAMES.get(status, str(status))
+        super().__init__(f"{self.status_name}: {message}")
+
+
+class flycoo_params(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_uint64 * MAX_MODES), ("g", ctypes.c_uint64), ("bins", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32)]
+
+
+class flycoo_info(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int32), ("layout_mode", ctypes.c_int32), ("nnz", ctypes.c_uint64),
+                ("dims", ctypes.c_uint64 * MAX_MODES), ("m", ctypes.c_uint64 * MAX_MODES),
+                ("g", ctypes.c_uint64), ("bins", ctypes.c_uint32), ("elem_bytes", ctypes.c_uint32),
+                ("super_shards", ctypes.c_uint64 * MAX_MODES), ("shards", ctypes.c_uint64 * MAX_MODES),
+                ("boundary_rows", ctypes.c_uint64 * MAX_MODES), ("device_bytes", ctypes.c_uint64)]
+
+
+_lib = None
+
+
+def lib():
+    """Load ``libflycoo.so`` (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libflycoo.so is not built ({LIB_PATH}); run __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        P, I, U64, U32 = ctypes.c_void_p, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint32
+        sigs = {
+            "flycoo_create": [I, P, U64, P, P, P, P, P],
+            "flycoo_destroy": [P],
+            "flycoo_spmttkrp": [P, I, P, I, I, P, I, P],
+            "flycoo_remap": [P, I, P],
+            "flycoo_get_info": [P, P],
+            "flycoo_export_layout": [P, P, P, P],
+            "flycoo_export_partition": [P, I, P, P, P, P],
+            "flycoo_export_schedule": [P, I, I, P, P],
+            "flycoo_export_next": [P, I, P, P],
+            "flycoo_timing_enable": [P, I],
+            "flycoo_timing_read": [P, P, P],
+            "flycoo_last_error": [],
+        }
+        for name, args in sigs.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = ctypes.c_int
+        L.flycoo_destroy.restype = None
+        L.flycoo_last_error.restype = ctypes.c_char_p
+        _lib = L
+    return _lib
+
+
+def flycoo_last_error() -> str:
+    return lib().flycoo_last_error().decode()
+
+
+def _check(status: int):
+    if status != OK:
+        raise FlycooError(status, flycoo_last_error())
+
+
+def _stream(stream) -> ctypes.c_void_p:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    if isinstance(stream, torch.cuda.Stream):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+def _dev_ptr(t: torch.Tensor, dtypes, what: str) -> ctypes.c_void_p:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{what} must be a CUDA tensor")
+    if t.dtype not in dtypes:
+        raise TypeError(f"{what} has dtype {t.dtype}, expected one of {dtypes}")
+    if not t.is_contiguous():
+        raise ValueError(f"{what} must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def make_params(m: Optional[Sequence[int]] = None, g: int = 0, bins: int = 0) -> flycoo_params:
+    p = flycoo_params()
+    for i, v in enumerate(m or []):
+        p.m[i] = int(v)
+    p.g = int(g)
+    p.bins = int(bins)
+    return p
+
+
+def flycoo_create(N: int, dims: Sequence[int], nnz: int, idx: torch.Tensor, vals: torch.Tensor,
+                  params: Optional[flycoo_params] = None, stream=None) -> ctypes.c_void_p:
+    """``idx``: int32/uint32 CUDA tensor [N, nnz] (mode-major); ``vals`` float32 [nnz]."""
+    h = ctypes.c_void_p()
+    d = (ctypes.c_uint64 * len(dims))(*[int(x) for x in dims])
+    pi = _dev_ptr(idx, (torch.int32, getattr(torch, "uint32", torch.int32)), "idx") if nnz else None
+    pv = _dev_ptr(vals, (torch.float32,), "vals") if nnz else None
+    if nnz and (idx.numel() != N * nnz or vals.numel() != nnz):
+        raise ValueError("idx must hold N*nnz coordinates and vals nnz values")
+    _check(lib().flycoo_create(int(N), d, int(nnz), pi, pv,
+                               ctypes.byref(params) if params is not None else None, _stream(stream),
+                               ctypes.byref(h)))
+    return h
+
+
+def flycoo_destroy(h) -> None:
+    if h:
+        lib().flycoo_destroy(h)
+
+
+def flycoo_spmttkrp(h, mode: int, factors: Sequence[Optional[torch.Tensor]], out: torch.Tensor,
+                    next_mode: int = -1, stream=None) -> None:
+    """``factors``: one CUDA tensor [I_w, R] per mode (float32 or bfloat16; the
+    entry of ``mode`` may be None); ``out``: float32 [I_mode, R]."""
+    N = len(factors)
+    ptrs = (ctypes.c_void_p * N)()
+    fdt = None
+    R = None
+    for w, f in enumerate(factors):
+        if w == mode or f is None:
+            continue
+        ptrs[w] = _dev_ptr(f, (torch.float32, torch.bfloat16), f"factor {w}")
+        dt = BF16 if f.dtype == torch.bfloat16 else F32
+        if fdt is not None and dt != fdt:
+            raise TypeError("all factors must share one dtype")
+        fdt = dt
+        if f.dim() != 2 or (R is not None and f.shape[1] != R):
+            raise ValueError("factors must be 2-D with a common rank")
+        R = f.shape[1]
+    if R is None:
+        raise ValueError("no input factor given")
+    po = _dev_ptr(out, (torch.float32,), "out")
+    if out.dim() != 2 or out.shape[1] != R:
+        raise ValueError("out must be [I_mode, R]")
+    _check(lib().flycoo_spmttkrp(h, int(mode), ptrs, int(fdt), int(R), po, int(next_mode), _stream(stream)))
+
+
+def flycoo_remap(h, next_mode: int, stream=None) -> None:
+    _check(lib().flycoo_remap(h, int(next_mode), _stream(stream)))
+
+
+def flycoo_get_info(h) -> dict:
+    info = flycoo_info()
+    _check(lib().flycoo_get_info(h, ctypes.byref(info)))
+    N = info.N
+    return dict(N=N, layout_mode=info.layout_mode, nnz=info.nnz, dims=list(info.dims[:N]),
+                m=list(info.m[:N]), g=info.g, bins=info.bins, elem_bytes=info.elem_bytes,
+                super_shards=list(info.super_shards[:N]), shards=list(info.shards[:N]),
+                boundary_rows=list(info.boundary_rows[:N]), device_bytes=info.device_bytes)
+
+
+def flycoo_export_layout(h, stream=None):
+    inf = flycoo_get_info(h)
+    N, nnz = inf["N"], inf["nnz"]
+    idx = torch.empty((N, nnz), dtype=torch.int32, device="cuda")
+    vals = torch.empty(nnz, dtype=torch.float32, device="cuda")
+    _check(lib().flycoo_export_layout(h, ctypes.c_void_p(idx.data_ptr()), ctypes.c_void_p(vals.data_ptr()),
+                                      _stream(stream)))
+    return idx, vals
+
+
+def flycoo_export_partition(h, mode: int):
+    inf = flycoo_get_info(h)
+    k, S = inf["super_shards"][mode], inf["shards"][mode]
+    ss = np.empty(k + 1, dtype=np.uint64)
+    sp = np.empty(S + 1, dtype=np.uint64)
+    fr = np.empty(S, dtype=np.uint32)
+    lr = np.empty(S, dtype=np.uint32)
+    _check(lib().flycoo_export_partition(h, int(mode), ss.ctypes.data, sp.ctypes.data, fr.ctypes.data,
+                                         lr.ctypes.data))
+    return ss, sp, fr, lr
+
+
+def flycoo_export_schedule(h, mode: int, which: int):
+    inf = flycoo_get_info(h)
+    n_items = inf["super_shards"][mode] if which == 0 else inf["shards"][mode]
+    bp = np.empty(inf["bins"] + 1, dtype=np.uint64)
+    it = np.empty(n_items, dtype=np.uint64)
+    _check(lib().flycoo_export_schedule(h, int(mode), int(which), bp.ctypes.data, it.ctypes.data))
+    return bp, it
+
+
+def flycoo_export_next(h, mode: int, stream=None) -> torch.Tensor:
+    nnz = flycoo_get_info(h)["nnz"]
+    nx = torch.empty(nnz, dtype=torch.int32, device="cuda")
+    _check(lib().flycoo_export_next(h, int(mode), ctypes.c_void_p(nx.data_ptr()), _stream(stream)))
+    return nx
+
+
+def flycoo_timing_enable(h, enable: bool = True) -> None:
+    _check(lib().flycoo_timing_enable(h, 1 if enable else 0))
+
+
+def flycoo_timing_read(h):
+    ms = ctypes.c_double()
+    n = ctypes.c_uint64()
+    _check(lib().flycoo_timing_read(h, ctypes.byref(ms), ctypes.byref(n)))
+    return ms.value, n.value
+
+
+def header_functions(header: Optional[str] = None) -> List[str]:
+    """Names of the functions ``include/flycoo.h`` declares."""
+    import re
+    header = header or os.path.join(os.path.dirname(HERE), "include", "flycoo.h")
+    src = open(header).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(flycoo_[a-z_0-9]+)\s*\(", src)))

@@ -1,0 +1,492 @@
+// api.cu -- the C ABI of include/flycoo.h: argument checks, the host-side
+// FLYCOO bookkeeping (Section III-A pointers, Algorithm 3 schedules,
+// boundary-row lists) and the dispatch of the kernels.
+#include "fused.cuh"
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <functional>
+#include <memory>
+#include <numeric>
+#include <queue>
+
+namespace flycoo {
+
+static thread_local std::string g_last_error;
+
+void set_error(const char *fmt, ...) {
+    char buf[1024];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+}
+
+void clear_error() { g_last_error.clear(); }
+
+u64 Tensor::device_bytes() const {
+    u64 b = elem[0].bytes + elem[1].bytes + partials.bytes;
+    for (int n = 0; n < N; ++n) {
+        const ModeMeta &m = mode[n];
+        b += m.d_shard_ptr.bytes + m.d_first_row.bytes + m.d_last_row.bytes + m.d_bin_ptr.bytes +
+             m.d_items.bytes + m.d_bnd.bytes + m.d_next.bytes;
+    }
+    return b;
+}
+
+bool fused_supported(int N, int R, flycoo_dtype dt) {
+    return N >= 3 && N <= 5 && (R == 16 || R == 32 || R == 64) && (dt == FLYCOO_F32 || dt == FLYCOO_BF16);
+}
+
+flycoo_status launch_fused(int N, int R, flycoo_dtype dt, const FusedArgs &a, cudaStream_t s) {
+    switch (N) {
+    case 3: return launch_fused_n3(R, dt, a, s);
+    case 4: return launch_fused_n4(R, dt, a, s);
+    case 5: return launch_fused_n5(R, dt, a, s);
+    default: break;
+    }
+    set_error("N = %d not built (3, 4 or 5)", N);
+    return FLYCOO_ERR_UNSUPPORTED;
+}
+
+// Algorithm 3: items sorted by size, descending (ties: ascending id); each goes
+// to the least-loaded bin (ties: lowest bin index).  CSR output, bins in
+// assignment order.
+static void lpt_schedule(const std::vector<u64> &size, u32 bins, std::vector<u32> &bin_ptr,
+                         std::vector<u32> &items) {
+    std::vector<u32> order(size.size());
+    std::iota(order.begin(), order.end(), 0u);
+    std::stable_sort(order.begin(), order.end(), [&](u32 a, u32 b) { return size[a] > size[b]; });
+    using P = std::pair<u64, u32>;
+    std::priority_queue<P, std::vector<P>, std::greater<P>> heap;
+    for (u32 b = 0; b < bins; ++b) heap.push({0, b});
+    std::vector<u32> bin_of(size.size());
+    std::vector<u32> count(bins, 0);
+    for (u32 it : order) {
+        P top = heap.top();
+        heap.pop();
+        bin_of[it] = top.second;
+        ++count[top.second];
+        heap.push({top.first + size[it], top.second});
+    }
+    bin_ptr.assign(bins + 1, 0);
+    for (u32 b = 0; b < bins; ++b) bin_ptr[b + 1] = bin_ptr[b] + count[b];
+    items.assign(size.size(), 0);
+    std::vector<u32> fill(bin_ptr.begin(), bin_ptr.end() - 1);
+    for (u32 it : order) items[fill[bin_of[it]]++] = it;
+}
+
+template <class T>
+static flycoo_status upload(DevBuf &d, const std::vector<T> &h, cudaStream_t s) {
+    FLY_TRY(d.alloc(std::max<size_t>(h.size() * sizeof(T), 16)));
+    if (!h.empty()) FLY_TRY_CUDA(cudaMemcpyAsync(d.p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+    return FLYCOO_OK;
+}
+
+// Section III-A pointers of one mode from its row pointers, plus the shard
+// rows, both schedules and the boundary-row list of K4.
+static flycoo_status partition_mode(Tensor &t, int n, const std::vector<u32> &rp, cudaStream_t s) {
+    ModeMeta &md = t.mode[n];
+    const u64 I = t.dims[n];
+    md.I = I;
+    md.k = (I + md.m - 1) / md.m;
+    md.ss_ptr.resize(md.k + 1);
+    for (u64 j = 0; j <= md.k; ++j) md.ss_ptr[j] = rp[std::min<u64>(j * md.m, I)];
+    md.shard_ptr.clear();
+    std::vector<u64> ss_shards(md.k);
+    for (u64 j = 0; j < md.k; ++j) {
+        const u64 size = md.ss_ptr[j + 1] - md.ss_ptr[j];
+        ss_shards[j] = (size + t.g - 1) / t.g;
+        for (u64 q = 0; q * t.g < size; ++q) md.shard_ptr.push_back((u32)(md.ss_ptr[j] + q * t.g));
+    }
+    md.S = md.shard_ptr.size();
+    md.shard_ptr.push_back((u32)t.nnz);
+    // row of a position: rp[r] <= p < rp[r+1]
+    auto row_of = [&](u64 p) -> u32 {
+        return (u32)(std::upper_bound(rp.begin(), rp.end(), (u32)p) - rp.begin() - 1);
+    };
+    md.first_row.resize(md.S);
+    md.last_row.resize(md.S);
+    std::vector<u64> shard_size(md.S);
+    for (u64 q = 0; q < md.S; ++q) {
+        md.first_row[q] = row_of(md.shard_ptr[q]);
+        md.last_row[q] = row_of(md.shard_ptr[q + 1] - 1);
+        shard_size[q] = md.shard_ptr[q + 1] - md.shard_ptr[q];
+    }
+    lpt_schedule(ss_shards, t.bins, md.ss_bin_ptr, md.ss_items);
+    lpt_schedule(shard_size, t.bins, md.sh_bin_ptr, md.sh_items);
+    // boundary rows: distinct first/last rows of the shards with their shard range
+    md.bnd.clear();
+    for (u64 q = 0; q < md.S; ++q) {
+        const u32 rows2[2] = {md.first_row[q], md.last_row[q]};
+        for (int i = 0; i < 2; ++i) {
+            if (i == 1 && rows2[1] == rows2[0]) break;
+            const size_t nb = md.bnd.size() / 3;
+            if (nb && md.bnd[3 * (nb - 1)] == rows2[i]) md.bnd[3 * (nb - 1) + 2] = (u32)q;
+            else {
+                md.bnd.push_back(rows2[i]);
+                md.bnd.push_back((u32)q);
+                md.bnd.push_back((u32)q);
+            }
+        }
+    }
+    FLY_TRY(upload(md.d_shard_ptr, md.shard_ptr, s));
+    FLY_TRY(upload(md.d_first_row, md.first_row, s));
+    FLY_TRY(upload(md.d_last_row, md.last_row, s));
+    FLY_TRY(upload(md.d_bin_ptr, md.sh_bin_ptr, s));
+    FLY_TRY(upload(md.d_items, md.sh_items, s));
+    FLY_TRY(upload(md.d_bnd, md.bnd, s));
+    return FLYCOO_OK;
+}
+
+flycoo_status launch_fixup(int R, const FixupArgs &a, cudaStream_t s) {
+    if (a.nb == 0) return FLYCOO_OK;
+    const unsigned blocks = (a.nb + 7) / 8;
+    switch (R) {
+    case 16: boundary_fixup_kernel<16><<<blocks, 256, 0, s>>>(a); break;
+    case 32: boundary_fixup_kernel<32><<<blocks, 256, 0, s>>>(a); break;
+    case 64: boundary_fixup_kernel<64><<<blocks, 256, 0, s>>>(a); break;
+    default: set_error("rank %d not built", R); return FLYCOO_ERR_UNSUPPORTED;
+    }
+    FLY_TRY_CUDA(cudaGetLastError());
+    return FLYCOO_OK;
+}
+
+// Keeps the caller's current device and switches to the handle's device.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) {
+            ok = false;
+            return;
+        }
+        if (prev != dev && cudaSetDevice(dev) != cudaSuccess) ok = false;
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+} // namespace flycoo
+
+using namespace flycoo;
+
+// --------------------------------------------------------------------------
+// the C ABI
+// --------------------------------------------------------------------------
+extern "C" const char *flycoo_last_error(void) { return g_last_error.c_str(); }
+
+extern "C" flycoo_status flycoo_create(int N, const uint64_t *h_dims, uint64_t nnz, const uint32_t *d_idx,
+                                       const float *d_vals, const flycoo_params *params,
+                                       flycoo_stream_t stream, flycoo_handle *out) {
+    clear_error();
+    if (!out) {
+        set_error("flycoo_create: out is NULL");
+        return FLYCOO_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    if (N < 1 || N > FLYCOO_MAX_MODES || !h_dims) {
+        set_error("flycoo_create: N must be in [1, %d] with dims given", FLYCOO_MAX_MODES);
+        return FLYCOO_ERR_INVALID_ARG;
+    }
+    if (N < 3 || N > 5) {
+        set_error("flycoo_create: N = %d not built (3, 4 or 5)", N);
+        return FLYCOO_ERR_UNSUPPORTED;
+    }
+    for (int w = 0; w < N; ++w)
+        if (h_dims[w] == 0 || h_dims[w] > 0xffffffffull) {
+            set_error("flycoo_create: dims[%d] = %llu outside [1, 2^32-1]", w, (unsigned long long)h_dims[w]);
+            return FLYCOO_ERR_INVALID_ARG;
+        }
+    if (nnz >= 0xffffffffull) {
+        set_error("flycoo_create: nnz must be < 2^32 - 1");
+        return FLYCOO_ERR_UNSUPPORTED;
+    }
+    if (nnz && (!d_idx || !d_vals)) {
+        set_error("flycoo_create: d_idx / d_vals is NULL");
+        return FLYCOO_ERR_INVALID_ARG;
+    }
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    auto t = std::make_unique<flycoo_tensor>();
+    FLY_TRY_CUDA(cudaGetDevice(&t->device));
+    FLY_TRY_CUDA(cudaDeviceGetAttribute(&t->sm_count, cudaDevAttrMultiProcessorCount, t->device));
+    t->N = N;
+    t->nnz = nnz;
+    for (int w = 0; w < N; ++w) t->dims[w] = h_dims[w];
+    t->bins = (params && params->bins) ? params->bins : (u32)(4 * t->sm_count);
+    if (params && params->g) {
+        t->g = params->g;
+    } else {
+        u64 g = 8192;
+        while (g > 256 && nnz / g < 4ull * t->bins) g >>= 1;
+        t->g = g;
+    }
+    if (t->g > 0xffffffffull) {
+        set_error("flycoo_create: g too large");
+        return FLYCOO_ERR_INVALID_ARG;
+    }
+    for (int w = 0; w < N; ++w) {
+        u64 m = (params && params->m[w]) ? params->m[w] : (h_dims[w] + t->bins - 1) / t->bins;
+        t->mode[w].m = std::max<u64>(m, 1);
+    }
+    t->elem_words = elem_words_for(N);
+
+    std::vector<std::vector<u32>> row_ptr;
+    FLY_TRY(build_flycoo(*t, d_idx, d_vals, row_ptr, s));
+    for (int n = 0; n < N; ++n) {
+        FLY_TRY(partition_mode(*t, n, row_ptr[n], s));
+        t->max_S = std::max<u64>(t->max_S, t->mode[n].S);
+    }
+    FLY_TRY(t->partials.alloc(2 * std::max<u64>(t->max_S, 1) * kMaxRank * sizeof(float)));
+    FLY_TRY_CUDA(cudaStreamSynchronize(s));
+    *out = t.release();
+    return FLYCOO_OK;
+}
+
+extern "C" void flycoo_destroy(flycoo_handle h) {
+    if (!h) return;
+    DeviceGuard dg(h->device);
+    for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+    delete h;
+}
+
+static flycoo_status next_event_pair(Tensor &t, cudaEvent_t *a, cudaEvent_t *b) {
+    while (t.ev_pool.size() < t.ev_used + 2) {
+        cudaEvent_t e;
+        FLY_TRY_CUDA(cudaEventCreate(&e));
+        t.ev_pool.push_back(e);
+    }
+    *a = t.ev_pool[t.ev_used++];
+    *b = t.ev_pool[t.ev_used++];
+    return FLYCOO_OK;
+}
+
+extern "C" flycoo_status flycoo_spmttkrp(flycoo_handle h, int mode, const void *const *h_factors,
+                                         flycoo_dtype fdt, int R, float *d_out, int next_mode,
+                                         flycoo_stream_t stream) {
+    clear_error();
+    if (!h) {
+        set_error("flycoo_spmttkrp: handle is NULL");
+        return FLYCOO_ERR_INVALID_ARG;
+    }
+    Tensor &t = *h;
+    if (mode < 0 || mode >= t.N) {
+        set_error("flycoo_spmttkrp: mode %d outside [0, %d)", mode, t.N);
+        return FLYCOO_ERR_INVALID_ARG;
+    }
+    if (fdt != FLYCOO_F32 && fdt != FLYCOO_BF16) {
+        set_error("flycoo_spmttkrp: unknown factor dtype %d", (int)fdt);
+        return FLYCOO_ERR_INVALID_ARG;
+    }
+    if (R != 16 && R != 32 && R != 64) {
+        set_error("flycoo_spmttkrp: rank %d not built (16, 32 or 64)", R);
+        return R > 0 ? FLYCOO_ERR_UNSUPPORTED : FLYCOO_ERR_INVALID_ARG;
+    }
+    if (next_mode != -1 && next_mode != (mode + 1) % t.N) {
+        set_error("flycoo_spmttkrp: next_mode must be -1 or (mode+1) mod N = %d", (mode + 1) % t.N);
+        return FLYCOO_ERR_INVALID_ARG;
+    }
+    if (!d_out || (reinterpret_cast<uintptr_t>(d_out) & 15u)) {
+        set_error("flycoo_spmttkrp: d_out is NULL or not 16-byte aligned");
+        return FLYCOO_ERR_INVALID_ARG;
+    }
+    if (!h_factors) {
+        set_error("flycoo_spmttkrp: h_factors is NULL");
+        return FLYCOO_ERR_INVALID_ARG;
+    }
+    for (int w = 0; w < t.N; ++w) {
+        if (w == mode) continue;
+        if (!h_factors[w] || (reinterpret_cast<uintptr_t>(h_factors[w]) & 15u)) {
+            set_error("flycoo_spmttkrp: factor %d is NULL or not 16-byte aligned", w);
+            return FLYCOO_ERR_INVALID_ARG;
+        }
+    }
+    if (t.layout != mode) {
+        set_error("flycoo_spmttkrp: tensor is in layout L_%d, mode %d needs L_%d", t.layout, mode, mode);
+        return FLYCOO_ERR_LAYOUT;
+    }
+    DeviceGuard dg(t.device);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const ModeMeta &md = t.mode[mode];
+    if (t.nnz == 0) {
+        FLY_TRY_CUDA(cudaMemsetAsync(d_out, 0, (size_t)t.dims[mode] * R * sizeof(float), s));
+        if (next_mode >= 0) t.layout = next_mode;
+        return FLYCOO_OK;
+    }
+    FusedArgs a{};
+    a.elem_in = t.elem[t.cur].p;
+    a.elem_out = next_mode >= 0 ? t.elem[1 - t.cur].p : nullptr;
+    a.next = next_mode >= 0 ? md.d_next.as<u32>() : nullptr;
+    for (int q = 1; q < t.N; ++q) a.Y[q - 1] = h_factors[(mode + q) % t.N];
+    a.out = d_out;
+    a.shard_ptr = md.d_shard_ptr.as<u32>();
+    a.first_row = md.d_first_row.as<u32>();
+    a.last_row = md.d_last_row.as<u32>();
+    a.bin_ptr = md.d_bin_ptr.as<u32>();
+    a.bin_items = md.d_items.as<u32>();
+    a.p_head = t.partials.as<float>();
+    a.p_tail = t.partials.as<float>() + t.max_S * kMaxRank;
+    a.I_out = (u32)t.dims[mode];
+    a.S = (u32)md.S;
+    a.bins = t.bins;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (t.timing) {
+        FLY_TRY(next_event_pair(t, &e0, &e1));
+        FLY_TRY_CUDA(cudaEventRecord(e0, s));
+    }
+    FLY_TRY(launch_fused(t.N, R, fdt, a, s));
+    if (t.timing) {
+        FLY_TRY_CUDA(cudaEventRecord(e1, s));
+        t.ev_pending.push_back({e0, e1});
+    }
+    FixupArgs f{};
+    f.bnd = md.d_bnd.as<u32>();
+    f.nb = (u32)(md.bnd.size() / 3);
+    f.first_row = md.d_first_row.as<u32>();
+    f.p_head = a.p_head;
+    f.p_tail = a.p_tail;
+    f.out = d_out;
+    FLY_TRY(launch_fixup(R, f, s));
+    if (next_mode >= 0) {
+        t.cur = 1 - t.cur;
+        t.layout = next_mode;
+    }
+    return FLYCOO_OK;
+}
+
+extern "C" flycoo_status flycoo_remap(flycoo_handle h, int next_mode, flycoo_stream_t stream) {
+    clear_error();
+    if (!h || next_mode < 0 || next_mode >= h->N) {
+        set_error("flycoo_remap: bad handle or next_mode");
+        return FLYCOO_ERR_INVALID_ARG;
+    }
+    Tensor &t = *h;
+    DeviceGuard dg(t.device);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    while (t.layout != next_mode) {
+        FLY_TRY(launch_remap_step(t, t.layout, t.elem[t.cur].p, t.elem[1 - t.cur].p, s));
+        t.cur = 1 - t.cur;
+        t.layout = (t.layout + 1) % t.N;
+    }
+    return FLYCOO_OK;
+}
+
+extern "C" flycoo_status flycoo_get_info(flycoo_handle h, flycoo_info *out) {
+    clear_error();
+    if (!h || !out) {
+        set_error("flycoo_get_info: NULL argument");
+        return FLYCOO_ERR_INVALID_ARG;
+    }
+    const Tensor &t = *h;
+    std::memset(out, 0, sizeof *out);
+    out->N = t.N;
+    out->layout_mode = t.layout;
+    out->nnz = t.nnz;
+    out->g = t.g;
+    out->bins = t.bins;
+    out->elem_bytes = (uint32_t)(t.elem_words * 4);
+    for (int n = 0; n < t.N; ++n) {
+        out->dims[n] = t.dims[n];
+        out->m[n] = t.mode[n].m;
+        out->super_shards[n] = t.mode[n].k;
+        out->shards[n] = t.mode[n].S;
+        out->boundary_rows[n] = t.mode[n].bnd.size() / 3;
+    }
+    out->device_bytes = t.device_bytes();
+    return FLYCOO_OK;
+}
+
+extern "C" flycoo_status flycoo_export_layout(flycoo_handle h, uint32_t *d_idx_out, float *d_vals_out,
+                                              flycoo_stream_t stream) {
+    clear_error();
+    if (!h || (h->nnz && (!d_idx_out || !d_vals_out))) {
+        set_error("flycoo_export_layout: NULL argument");
+        return FLYCOO_ERR_INVALID_ARG;
+    }
+    DeviceGuard dg(h->device);
+    return launch_export_layout(*h, h->elem[h->cur].p, d_idx_out, d_vals_out,
+                                reinterpret_cast<cudaStream_t>(stream));
+}
+
+extern "C" flycoo_status flycoo_export_partition(flycoo_handle h, int mode, uint64_t *h_ss_ptr,
+                                                 uint64_t *h_shard_ptr, uint32_t *h_first_row,
+                                                 uint32_t *h_last_row) {
+    clear_error();
+    if (!h || mode < 0 || mode >= h->N) {
+        set_error("flycoo_export_partition: bad handle or mode");
+        return FLYCOO_ERR_INVALID_ARG;
+    }
+    const ModeMeta &md = h->mode[mode];
+    if (h_ss_ptr) std::copy(md.ss_ptr.begin(), md.ss_ptr.end(), h_ss_ptr);
+    if (h_shard_ptr)
+        for (size_t i = 0; i < md.shard_ptr.size(); ++i) h_shard_ptr[i] = md.shard_ptr[i];
+    if (h_first_row) std::copy(md.first_row.begin(), md.first_row.end(), h_first_row);
+    if (h_last_row) std::copy(md.last_row.begin(), md.last_row.end(), h_last_row);
+    return FLYCOO_OK;
+}
+
+extern "C" flycoo_status flycoo_export_schedule(flycoo_handle h, int mode, int which, uint64_t *h_bin_ptr,
+                                                uint64_t *h_items) {
+    clear_error();
+    if (!h || mode < 0 || mode >= h->N || (which != 0 && which != 1)) {
+        set_error("flycoo_export_schedule: bad handle, mode or which");
+        return FLYCOO_ERR_INVALID_ARG;
+    }
+    const ModeMeta &md = h->mode[mode];
+    const std::vector<u32> &bp = which == 0 ? md.ss_bin_ptr : md.sh_bin_ptr;
+    const std::vector<u32> &it = which == 0 ? md.ss_items : md.sh_items;
+    if (h_bin_ptr)
+        for (size_t i = 0; i < bp.size(); ++i) h_bin_ptr[i] = bp[i];
+    if (h_items)
+        for (size_t i = 0; i < it.size(); ++i) h_items[i] = it[i];
+    return FLYCOO_OK;
+}
+
+extern "C" flycoo_status flycoo_export_next(flycoo_handle h, int mode, uint32_t *d_next,
+                                            flycoo_stream_t stream) {
+    clear_error();
+    if (!h || mode < 0 || mode >= h->N || (h->nnz && !d_next)) {
+        set_error("flycoo_export_next: bad argument");
+        return FLYCOO_ERR_INVALID_ARG;
+    }
+    if (h->nnz == 0) return FLYCOO_OK;
+    DeviceGuard dg(h->device);
+    FLY_TRY_CUDA(cudaMemcpyAsync(d_next, h->mode[mode].d_next.p, h->nnz * 4, cudaMemcpyDeviceToDevice,
+                                 reinterpret_cast<cudaStream_t>(stream)));
+    return FLYCOO_OK;
+}
+
+extern "C" flycoo_status flycoo_timing_enable(flycoo_handle h, int enable) {
+    clear_error();
+    if (!h) {
+        set_error("flycoo_timing_enable: handle is NULL");
+        return FLYCOO_ERR_INVALID_ARG;
+    }
+    h->timing = enable != 0;
+    return FLYCOO_OK;
+}
+
+extern "C" flycoo_status flycoo_timing_read(flycoo_handle h, double *h_ms, uint64_t *h_launches) {
+    clear_error();
+    if (!h) {
+        set_error("flycoo_timing_read: handle is NULL");
+        return FLYCOO_ERR_INVALID_ARG;
+    }
+    DeviceGuard dg(h->device);
+    double total = 0.0;
+    for (auto &pr : h->ev_pending) {
+        FLY_TRY_CUDA(cudaEventSynchronize(pr.second));
+        float ms = 0.f;
+        FLY_TRY_CUDA(cudaEventElapsedTime(&ms, pr.first, pr.second));
+        total += ms;
+    }
+    if (h_ms) *h_ms = total;
+    if (h_launches) *h_launches = h->ev_pending.size();
+    h->ev_pending.clear();
+    h->ev_used = 0;
+    return FLYCOO_OK;
+}

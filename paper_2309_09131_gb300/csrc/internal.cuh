@@ -1,0 +1,163 @@
+// internal.cuh -- shared declarations of the FLYCOO CUDA library (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "flycoo.h"
+
+namespace flycoo {
+
+using u32 = uint32_t;
+using u64 = uint64_t;
+
+// --------------------------------------------------------------------------
+// errors
+// --------------------------------------------------------------------------
+void set_error(const char *fmt, ...);
+void clear_error();
+
+#define FLY_TRY_CUDA(call)                                                                    \
+    do {                                                                                      \
+        cudaError_t e__ = (call);                                                             \
+        if (e__ != cudaSuccess) {                                                             \
+            ::flycoo::set_error("%s failed: %s (%s:%d)", #call, cudaGetErrorString(e__),      \
+                                __FILE__, __LINE__);                                          \
+            return e__ == cudaErrorMemoryAllocation ? FLYCOO_ERR_OOM : FLYCOO_ERR_CUDA;       \
+        }                                                                                     \
+    } while (0)
+
+#define FLY_TRY(call)                                                                         \
+    do {                                                                                      \
+        flycoo_status s__ = (call);                                                           \
+        if (s__ != FLYCOO_OK) return s__;                                                     \
+    } while (0)
+
+// Owning device allocation (freed on destruction).
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf &) = delete;
+    DevBuf &operator=(const DevBuf &) = delete;
+    ~DevBuf() { release(); }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    flycoo_status alloc(size_t n) {
+        release();
+        if (n == 0) n = 16;
+        cudaError_t e = cudaMalloc(&p, n);
+        if (e != cudaSuccess) {
+            p = nullptr;
+            set_error("cudaMalloc(%zu) failed: %s", n, cudaGetErrorString(e));
+            return e == cudaErrorMemoryAllocation ? FLYCOO_ERR_OOM : FLYCOO_ERR_CUDA;
+        }
+        bytes = n;
+        return FLYCOO_OK;
+    }
+    template <class T> T *as() const { return static_cast<T *>(p); }
+};
+
+// --------------------------------------------------------------------------
+// FLYCOO description of one mode (Section III-A)
+// --------------------------------------------------------------------------
+struct ModeMeta {
+    u64 I = 0, m = 0, k = 0, S = 0;
+    std::vector<u64> ss_ptr;              // k + 1
+    std::vector<u32> shard_ptr;           // S + 1
+    std::vector<u32> first_row, last_row; // S
+    std::vector<u32> ss_bin_ptr, ss_items;  // Algorithm 3 over super-shards
+    std::vector<u32> sh_bin_ptr, sh_items;  // Algorithm 3 over shards (kernel schedule)
+    std::vector<u32> bnd;                   // boundary rows: (row, s_lo, s_hi) triples
+    DevBuf d_shard_ptr, d_first_row, d_last_row, d_bin_ptr, d_items, d_bnd, d_next;
+};
+
+struct Tensor {
+    int N = 0;
+    int device = 0;
+    int sm_count = 0;
+    u64 nnz = 0;
+    u64 dims[FLYCOO_MAX_MODES] = {};
+    u64 g = 0;
+    u32 bins = 0;
+    int layout = 0;     // current layout mode
+    int elem_words = 4; // 32-bit words per stored nonzero
+    int cur = 0;        // which element buffer holds the current layout
+    u64 max_S = 0;
+    DevBuf elem[2];
+    DevBuf partials;    // 2 x max_S x kMaxRank floats (head then tail)
+    ModeMeta mode[FLYCOO_MAX_MODES];
+    // kernel timing
+    bool timing = false;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending;
+    size_t ev_used = 0;
+    u64 device_bytes() const;
+};
+
+constexpr int kMaxRank = 64;
+constexpr u32 kInvalidRow = 0xffffffffu;
+
+inline int elem_words_for(int N) { return (N + 1 <= 4) ? 4 : 8; }
+
+// --------------------------------------------------------------------------
+// device building blocks (partition.cu)
+// --------------------------------------------------------------------------
+// exclusive scan of n uint32 values (in place allowed); scratch >= scan_scratch_words(n)
+u64 scan_scratch_words(u64 n);
+flycoo_status exclusive_scan_u32(const u32 *in, u32 *out, u64 n, u32 *scratch, cudaStream_t s);
+
+// K1: layouts, remap permutations, row pointers and the L_0 element buffer
+flycoo_status build_flycoo(Tensor &t, const u32 *d_idx, const float *d_vals,
+                           std::vector<std::vector<u32>> &row_ptr_host, cudaStream_t s);
+
+// standalone remap step L_n -> L_{n+1} (and layout export)
+flycoo_status launch_remap_step(const Tensor &t, int n, const void *in, void *out, cudaStream_t s);
+flycoo_status launch_export_layout(const Tensor &t, const void *elem, u32 *idx_out, float *vals_out,
+                                   cudaStream_t s);
+
+// --------------------------------------------------------------------------
+// fused spMTTKRP + remap (K2) and boundary-row fixup (K4)
+// --------------------------------------------------------------------------
+struct FusedArgs {
+    const void *elem_in;
+    void *elem_out;            // nullptr: no remap
+    const u32 *next;           // nullptr: no remap
+    const void *Y[FLYCOO_MAX_MODES - 1]; // factors of slots 1..N-1 of the current layout
+    float *out;
+    const u32 *shard_ptr, *first_row, *last_row;
+    const u32 *bin_ptr, *bin_items;
+    float *p_head, *p_tail;    // S x R each
+    u32 I_out;
+    u32 S;
+    u32 bins;
+};
+
+struct FixupArgs {
+    const u32 *bnd;    // triples (row, s_lo, s_hi)
+    u32 nb;
+    const u32 *first_row;
+    const float *p_head, *p_tail;
+    float *out;
+};
+
+flycoo_status launch_fused(int N, int R, flycoo_dtype dt, const FusedArgs &a, cudaStream_t s);
+flycoo_status launch_fixup(int R, const FixupArgs &a, cudaStream_t s);
+bool fused_supported(int N, int R, flycoo_dtype dt);
+
+// launchers implemented per mode count (fused_n3.cu, fused_n4.cu, fused_n5.cu)
+flycoo_status launch_fused_n3(int R, flycoo_dtype dt, const FusedArgs &a, cudaStream_t s);
+flycoo_status launch_fused_n4(int R, flycoo_dtype dt, const FusedArgs &a, cudaStream_t s);
+flycoo_status launch_fused_n5(int R, flycoo_dtype dt, const FusedArgs &a, cudaStream_t s);
+
+} // namespace flycoo
+
+// the opaque handle type of the C ABI
+struct flycoo_tensor : flycoo::Tensor {};

@@ -1,0 +1,86 @@
+"""Full-size parity on the Nell-2-sized workload (12,000 x 9,000 x 29,000,
+77M nonzeros, Zipf(1.1) indices, R = 32) in the launch configuration the
+benchmark times (default partition parameters): sampled output rows against
+the oracle row by row, and layout properties that hold at any size."""
+import numpy as np
+import pytest
+
+import oracle
+from synth import WORKLOADS, make_workload
+
+from _util import rel_fro, to_np
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+WL = WORKLOADS["nell2like_12000x9000x29000_77m_r32"]
+
+
+@pytest.fixture(scope="module")
+def data():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2309_09131_gb300 as P
+    idx, vals, facs = make_workload(WL)
+    T = P.FlycooTensor(idx, vals, WL.dims)
+    return P, T, idx, vals, facs
+
+
+def _sample_rows(idx_n, I, rng):
+    counts = np.bincount(idx_n, minlength=I)
+    heavy = np.argsort(counts)[-6:]
+    empty = np.nonzero(counts == 0)[0][:4]
+    rand = rng.choice(I, size=12, replace=False)
+    return np.unique(np.concatenate([heavy, empty, rand, [0, I - 1]])).astype(np.uint32)
+
+
+def test_sampled_rows_fp32_and_bf16(data):
+    P, T, idx, vals, facs = data
+    rng = np.random.default_rng(0)
+    Y64 = oracle.factors_f64(facs)
+    Yb64 = oracle.factors_f64(facs, bf16=True)
+    rows = [_sample_rows(idx[n], WL.dims[n], rng) for n in range(3)]
+    for dtype in (torch.float32, torch.bfloat16):
+        Y = [torch.from_numpy(f).cuda().to(dtype) for f in facs]
+        outs = T.all_modes(Y)
+        torch.cuda.synchronize()
+        for n in range(3):
+            got = to_np(outs[n])[rows[n]]
+            ref = oracle.mttkrp_rows(idx, vals, Y64, n, rows[n], WL.dims)
+            if dtype == torch.float32:
+                assert rel_fro(got, ref) <= 1e-5
+            else:
+                refb = oracle.mttkrp_rows(idx, vals, Yb64, n, rows[n], WL.dims)
+                assert rel_fro(got, refb) <= 1e-5
+                assert rel_fro(got, ref) <= 1e-2
+    assert T.layout_mode == 0
+
+
+def test_layout_properties_full_size(data):
+    P, T, idx, vals, facs = data
+    N = 3
+    for n in range(N):
+        if n:
+            T.remap(n)
+        li, lv = T.export_layout()
+        c = to_np(li).view(np.uint32)
+        # sorted by the cyclic key (c_n, c_{n-1}, c_{n+1}): compare adjacent positions
+        k0, k1, k2 = c[n].astype(np.int64), c[(n - 1) % N].astype(np.int64), c[(n + 1) % N].astype(np.int64)
+        d0, d1, d2 = np.diff(k0), np.diff(k1), np.diff(k2)
+        ok = (d0 > 0) | ((d0 == 0) & ((d1 > 0) | ((d1 == 0) & (d2 > 0))))
+        assert ok.all(), "layout not strictly ordered by the cyclic key (coordinates are distinct)"
+        if n == 0:
+            # a permutation of the input: same coordinates and values as a multiset
+            key_in = (idx[0].astype(np.int64) * WL.dims[1] + idx[1]) * WL.dims[2] + idx[2]
+            key_out = (c[0].astype(np.int64) * WL.dims[1] + c[1]) * WL.dims[2] + c[2]
+            o_in = np.argsort(key_in)
+            o_out = np.argsort(key_out)
+            np.testing.assert_array_equal(key_in[o_in], key_out[o_out])
+            np.testing.assert_array_equal(vals[o_in], to_np(lv)[o_out])
+    T.remap(0)
+    info = T.info
+    # Section III-A shard count: S_n = sum_j ceil(|SS_n,j| / g)
+    for n in range(N):
+        ss, sp, fr, lr = T.export_partition(n)
+        sizes = np.diff(ss.astype(np.int64))
+        assert info["shards"][n] == int(np.sum((sizes + info["g"] - 1) // info["g"]))

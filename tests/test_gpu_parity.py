@@ -1,0 +1,221 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Integer structures (layouts, pointers, remap permutations, schedules) must
+match bit for bit.  FP32 spMTTKRP must match within relative Frobenius error
+1e-5 per mode; BF16 factor storage within 1e-2 against the FP32 factors (and
+1e-5 against the same BF16-rounded factors, which isolates the FP32
+accumulation).  Where the data make every FP32 operation exact (unit factors,
+small integer values) the result must be bitwise equal.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from synth import make_factors, random_coo
+
+from _util import rel_fro, to_np
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+FP32_TOL = 1e-5
+BF16_TOL = 1e-2
+
+
+@pytest.fixture(scope="module")
+def P():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2309_09131_gb300 as pkg
+    pkg._native.lib()
+    return pkg
+
+
+def _cuda_factors(facs, dtype):
+    return [torch.from_numpy(f).to("cuda").to(dtype).contiguous() for f in facs]
+
+
+LAYOUT_CASES = [
+    # dims, nnz, seed, law, distinct, m, g, bins
+    ((30, 20, 10), 500, 0, "uniform", False, (3, 2, 4), 7, 5),
+    ((6, 5, 4, 3), 300, 1, "zipf", False, (1, 1, 1, 1), 16, 3),
+    ((4, 3, 3, 2, 2), 100, 2, "uniform", False, (2, 1, 1, 1, 1), 5, 4),
+    ((50, 2, 3), 150, 3, "zipf", True, (7, 1, 1), 1, 2),
+    ((1000, 800, 600), 20000, 4, "zipf", True, (0, 0, 0), 0, 0),
+    ((3, 1, 700), 700, 5, "uniform", True, (1, 1, 10), 64, 9),
+]
+
+
+@pytest.mark.parametrize("case", LAYOUT_CASES, ids=lambda c: f"{c[0]}-{c[1]}")
+def test_layout_partition_schedule_bitexact(P, case):
+    dims, nnz, seed, law, distinct, m, g, bins = case
+    idx, vals = random_coo(dims, nnz, seed=seed, law=law, distinct=distinct)
+    T = P.FlycooTensor(idx, vals, dims, m=m, g=g, bins=bins)
+    info = T.info
+    N = len(dims)
+    assert info["nnz"] == nnz and info["layout_mode"] == 0
+    ref = oracle.flycoo_layout(idx, dims, info["m"], info["g"], info["bins"])
+    for n in range(N):
+        ss, sp, fr, lr = T.export_partition(n)
+        np.testing.assert_array_equal(ss, ref[n]["ss_ptr"])
+        np.testing.assert_array_equal(sp, ref[n]["shard_ptr"])
+        np.testing.assert_array_equal(fr, ref[n]["first_row"])
+        np.testing.assert_array_equal(lr, ref[n]["last_row"])
+        for which, key in ((0, "ss_bins"), (1, "shard_bins")):
+            bp, items = T.export_schedule(n, which)
+            np.testing.assert_array_equal(bp, ref[n][key][0])
+            np.testing.assert_array_equal(items, ref[n][key][1])
+        np.testing.assert_array_equal(to_np(T.export_next(n)).view(np.uint32), ref[n]["next"])
+    # the stored tensor walks L_0 -> L_1 -> ... -> L_0 exactly
+    for step in range(N + 1):
+        n = step % N
+        if step:
+            T.remap(n)
+        li, lv = T.export_layout()
+        order = ref[n]["order"]
+        np.testing.assert_array_equal(to_np(li).view(np.uint32), idx[:, order])
+        np.testing.assert_array_equal(to_np(lv).view(np.uint32), vals[order].view(np.uint32))
+        assert T.layout_mode == n
+
+
+MTTKRP_CASES = [
+    # dims, nnz, law, R, g, bins
+    ((1000, 800, 600), 100_000, "uniform", 16, 0, 0),
+    ((200, 150, 120), 30_000, "zipf", 32, 512, 37),
+    ((300, 50, 400), 25_000, "zipf", 64, 1000, 64),
+    ((60, 70, 50, 40), 20_000, "zipf", 32, 700, 20),
+    ((40, 30, 20, 10, 9), 12_000, "uniform", 16, 300, 11),
+    ((40, 30, 20, 10, 9), 12_000, "zipf", 64, 333, 7),
+]
+
+
+@pytest.mark.parametrize("case", MTTKRP_CASES, ids=lambda c: f"{c[0]}-{c[1]}-R{c[3]}")
+def test_all_modes_fp32_and_bf16(P, case):
+    dims, nnz, law, R, g, bins = case
+    N = len(dims)
+    idx, vals = random_coo(dims, nnz, seed=11, law=law, distinct=True, value_law="lognormal")
+    facs = make_factors(dims, R, "normal", seed=11)
+    T = P.FlycooTensor(idx, vals, dims, g=g, bins=bins)
+    Y64 = oracle.factors_f64(facs)
+    Yb64 = oracle.factors_f64(facs, bf16=True)
+    for dtype in (torch.float32, torch.bfloat16):
+        outs = T.all_modes(_cuda_factors(facs, dtype))
+        torch.cuda.synchronize()
+        assert T.layout_mode == 0
+        for n in range(N):
+            got = to_np(outs[n])
+            ref = oracle.mttkrp(idx, vals, Y64, n, dims)
+            if dtype == torch.float32:
+                assert rel_fro(got, ref) <= FP32_TOL, (n, rel_fro(got, ref))
+            else:
+                refb = oracle.mttkrp(idx, vals, Yb64, n, dims)
+                assert rel_fro(got, refb) <= FP32_TOL, (n, rel_fro(got, refb))
+                assert rel_fro(got, ref) <= BF16_TOL, (n, rel_fro(got, ref))
+
+
+def test_unit_factors_integer_values_are_exact(P):
+    # every product is 1 * val and every partial sum an integer below 2^24
+    dims = (64, 48, 40)
+    idx, vals = random_coo(dims, 40_000, seed=3, law="zipf", distinct=False, value_law="int1to5")
+    T = P.FlycooTensor(idx, vals, dims, g=97, bins=13)
+    for dtype in (torch.float32, torch.bfloat16):
+        Y = [torch.ones((d, 32), dtype=dtype, device="cuda") for d in dims]
+        outs = T.all_modes(Y)
+        Y64 = [np.ones((d, 32)) for d in dims]
+        for n in range(3):
+            np.testing.assert_array_equal(to_np(outs[n]), oracle.mttkrp(idx, vals, Y64, n, dims))
+
+
+def test_heavy_row_spanning_many_shards(P):
+    # one output row holds most nonzeros: many shards, long fixed-order combine
+    rng = np.random.default_rng(5)
+    dims = (50, 400, 300)
+    nnz = 60_000
+    idx = np.stack([np.where(rng.random(nnz) < 0.8, 7, rng.integers(0, 50, nnz)),
+                    rng.integers(0, 400, nnz), rng.integers(0, 300, nnz)]).astype(np.uint32)
+    vals = rng.standard_normal(nnz).astype(np.float32)
+    facs = make_factors(dims, 32, "normal", seed=5)
+    T = P.FlycooTensor(idx, vals, dims, g=64, bins=40)
+    outs = T.all_modes(_cuda_factors(facs, torch.float32))
+    Y64 = oracle.factors_f64(facs)
+    for n in range(3):
+        got = to_np(outs[n])
+        ref = oracle.mttkrp(idx, vals, Y64, n, dims)
+        assert rel_fro(got, ref) <= FP32_TOL
+        np.testing.assert_allclose(got, ref, rtol=1e-4, atol=1e-4 * np.abs(ref).max())
+
+
+@pytest.mark.parametrize("nnz,g,bins", [(0, 0, 4), (1, 0, 4), (5, 1, 1), (33, 1, 64), (1000, 3, 2)])
+def test_edge_cases(P, nnz, g, bins):
+    dims = (9, 1, 13)
+    idx, vals = random_coo(dims, nnz, seed=nnz, distinct=False, value_law="normal")
+    facs = make_factors(dims, 16, "normal", seed=1)
+    T = P.FlycooTensor(idx, vals, dims, g=g, bins=bins)
+    outs = T.all_modes(_cuda_factors(facs, torch.float32))
+    Y64 = oracle.factors_f64(facs)
+    for n in range(3):
+        got = to_np(outs[n])
+        ref = oracle.mttkrp(idx, vals, Y64, n, dims)
+        np.testing.assert_allclose(got, ref, rtol=2e-6, atol=1e-6)
+        assert np.all(got[np.abs(ref).sum(1) == 0] == 0.0)
+
+
+def test_single_row_tensor(P):
+    dims = (1, 1, 5000)
+    idx = np.stack([np.zeros(5000), np.zeros(5000), np.arange(5000)]).astype(np.uint32)
+    vals = np.linspace(-1, 1, 5000).astype(np.float32)
+    facs = make_factors(dims, 16, "normal", seed=2)
+    T = P.FlycooTensor(idx, vals, dims, g=128, bins=8)
+    outs = T.all_modes(_cuda_factors(facs, torch.float32))
+    Y64 = oracle.factors_f64(facs)
+    for n in range(3):
+        assert rel_fro(to_np(outs[n]), oracle.mttkrp(idx, vals, Y64, n, dims)) <= FP32_TOL
+
+
+def test_without_remap_and_determinism(P):
+    dims = (120, 90, 70)
+    idx, vals = random_coo(dims, 20_000, seed=8, law="zipf")
+    facs = _cuda_factors(make_factors(dims, 32, seed=8), torch.float32)
+    T = P.FlycooTensor(idx, vals, dims, g=256, bins=17)
+    a = T.spmttkrp(0, facs, remap=False)
+    assert T.layout_mode == 0
+    b = T.spmttkrp(0, facs, remap=True)
+    assert T.layout_mode == 1
+    assert torch.equal(a, b)
+    first = [o.clone() for o in T.all_modes(facs)]
+    second = T.all_modes(facs)
+    for x, y in zip(first, second):
+        assert torch.equal(x, y)
+
+
+def test_error_statuses(P):
+    dims = (10, 10, 10)
+    idx, vals = random_coo(dims, 100, seed=1)
+    T = P.FlycooTensor(idx, vals, dims, g=16, bins=4)
+    facs = _cuda_factors(make_factors(dims, 32, seed=1), torch.float32)
+    out = torch.empty((10, 32), device="cuda")
+    nat = P._native
+    with pytest.raises(P.FlycooError) as e:
+        nat.flycoo_spmttkrp(T.h, 1, facs, out, -1)
+    assert e.value.status_name == "FLYCOO_ERR_LAYOUT"
+    with pytest.raises(P.FlycooError) as e:
+        nat.flycoo_spmttkrp(T.h, 3, facs + [facs[0]], out, -1)
+    assert e.value.status_name == "FLYCOO_ERR_INVALID_ARG"
+    with pytest.raises(P.FlycooError) as e:
+        nat.flycoo_spmttkrp(T.h, 0, facs, out, 2)
+    assert e.value.status_name == "FLYCOO_ERR_INVALID_ARG"
+    with pytest.raises(P.FlycooError) as e:
+        nat.flycoo_spmttkrp(T.h, 0, [f[:, :24].contiguous() for f in facs], out[:, :24].contiguous(), -1)
+    assert e.value.status_name == "FLYCOO_ERR_UNSUPPORTED"
+    flat = torch.empty(10 * 32 + 1, device="cuda")
+    with pytest.raises(P.FlycooError) as e:
+        nat.flycoo_spmttkrp(T.h, 0, facs, flat[1:].view(10, 32), -1)
+    assert e.value.status_name == "FLYCOO_ERR_INVALID_ARG"
+    bad = idx.copy()
+    bad[2, 17] = 10
+    with pytest.raises(P.FlycooError) as e:
+        P.FlycooTensor(bad, vals, dims)
+    assert e.value.status_name == "FLYCOO_ERR_INDEX_RANGE"
+    # the context is still usable after the rejected calls
+    T.all_modes(facs)
+    torch.cuda.synchronize()
