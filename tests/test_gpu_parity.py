@@ -142,7 +142,8 @@ def test_heavy_row_spanning_many_shards(P):
         got = to_np(outs[n])
         ref = oracle.mttkrp(idx, vals, Y64, n, dims)
         assert rel_fro(got, ref) <= FP32_TOL
-        np.testing.assert_allclose(got, ref, rtol=1e-4, atol=1e-4 * np.abs(ref).max())
+        mag = oracle.mttkrp(idx, np.abs(vals), [np.abs(y) for y in Y64], n, dims)
+        assert np.all(np.abs(got - ref) <= 1e-5 * mag + 1e-30)
 
 
 @pytest.mark.parametrize("nnz,g,bins", [(0, 0, 4), (1, 0, 4), (5, 1, 1), (33, 1, 64), (1000, 3, 2)])
@@ -153,11 +154,15 @@ def test_edge_cases(P, nnz, g, bins):
     T = P.FlycooTensor(idx, vals, dims, g=g, bins=bins)
     outs = T.all_modes(_cuda_factors(facs, torch.float32))
     Y64 = oracle.factors_f64(facs)
+    A64 = [np.abs(y) for y in Y64]
     for n in range(3):
         got = to_np(outs[n])
         ref = oracle.mttkrp(idx, vals, Y64, n, dims)
-        np.testing.assert_allclose(got, ref, rtol=2e-6, atol=1e-6)
-        assert np.all(got[np.abs(ref).sum(1) == 0] == 0.0)
+        # FP32 summation error is bounded by a multiple of eps32 * sum |terms|
+        mag = oracle.mttkrp(idx, np.abs(vals), A64, n, dims)
+        assert np.all(np.abs(got - ref) <= 1e-5 * mag + 1e-30)
+        assert rel_fro(got, ref) <= FP32_TOL
+        assert np.all(got[mag.sum(1) == 0] == 0.0)
 
 
 def test_single_row_tensor(P):
