@@ -134,6 +134,31 @@ flycoo_status flycoo_spmttkrp(flycoo_handle h, int mode, const void *const *h_fa
                               flycoo_stream_t stream);
 
 /* ------------------------------------------------------------------------ */
+/* flycoo_spmttkrp_static_scratch -- the paper has no counterpart; this is a  */
+/* library convenience.  Same computation, arguments, errors and results as   */
+/* flycoo_spmttkrp, but the call allocates nothing: the partial rows of the   */
+/* rows that straddle shard boundaries go to a fixed device array inside the  */
+/* library (8 MiB per GPU, held by every GPU that loads the library until the */
+/* process exits) instead of the scratch buffer flycoo_create allocated.      */
+/* It is meant for callers that must not allocate device memory at the point  */
+/* of the call, for example code running while another allocator owns the    */
+/* GPU's free memory, or code that must not enter cudaMalloc on a time-bound  */
+/* path.  The handle itself still comes from flycoo_create, which allocates.  */
+/*  - Limit: 2 x S_mode x R x 4 bytes must fit in 8 MiB (S_mode = shards of    */
+/*    the mode, see flycoo_get_info); larger requests return INVALID_ARG and   */
+/*    flycoo_last_error() gives both sizes.  A larger g lowers S_mode.         */
+/*  - The first call on a device looks up the array's device address with     */
+/*    that device current; make that first call before any stream capture.    */
+/*  - All calls on a device share the one array and it keeps the last call's  */
+/*    contents; nothing in it needs to start at zero (every partial row is     */
+/*    written before it is read in the same call).  Calls whose work overlaps  */
+/*    on the GPU (different streams, or different handles at once) race on it. */
+/* ------------------------------------------------------------------------ */
+flycoo_status flycoo_spmttkrp_static_scratch(flycoo_handle h, int mode, const void *const *h_factors,
+                                             flycoo_dtype fdt, int R, float *d_out, int next_mode,
+                                             flycoo_stream_t stream);
+
+/* ------------------------------------------------------------------------ */
 /* flycoo_remap -- dynamic tensor remapping alone (Section III-B): move the  */
 /* tensor from its current layout to L_next_mode.  Each step stores every    */
 /* nonzero at its slot of the following mode's layout; the call takes       */

@@ -18,6 +18,7 @@ from ._native import (  # noqa: F401
     flycoo_last_error,
     flycoo_remap,
     flycoo_spmttkrp,
+    flycoo_spmttkrp_static_scratch,
     flycoo_timing_enable,
     flycoo_timing_read,
     make_params,

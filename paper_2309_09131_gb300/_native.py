@@ -61,6 +61,7 @@ def lib():
             "flycoo_create": [I, P, U64, P, P, P, P, P],
             "flycoo_destroy": [P],
             "flycoo_spmttkrp": [P, I, P, I, I, P, I, P],
+            "flycoo_spmttkrp_static_scratch": [P, I, P, I, I, P, I, P],
             "flycoo_remap": [P, I, P],
             "flycoo_get_info": [P, P],
             "flycoo_export_layout": [P, P, P, P],
@@ -162,6 +163,39 @@ def flycoo_spmttkrp(h, mode: int, factors: Sequence[Optional[torch.Tensor]], out
     if out.dim() != 2 or out.shape[1] != R:
         raise ValueError("out must be [I_mode, R]")
     _check(lib().flycoo_spmttkrp(h, int(mode), ptrs, int(fdt), int(R), po, int(next_mode), _stream(stream)))
+
+
+def flycoo_spmttkrp_static_scratch(h, mode: int, factors: Sequence[Optional[torch.Tensor]],
+                                   out: torch.Tensor, next_mode: int = -1, stream=None) -> None:
+    """As ``flycoo_spmttkrp``, with the partial rows in the library's fixed
+    8 MiB device array; the call allocates nothing (see include/flycoo.h)."""
+    ptrs, fdt, R, po = _spmttkrp_args(mode, factors, out)
+    _check(lib().flycoo_spmttkrp_static_scratch(h, int(mode), ptrs, int(fdt), int(R), po, int(next_mode),
+                                                _stream(stream)))
+
+
+def _spmttkrp_args(mode, factors, out):
+    N = len(factors)
+    ptrs = (ctypes.c_void_p * N)()
+    fdt = None
+    R = None
+    for w, f in enumerate(factors):
+        if w == mode or f is None:
+            continue
+        ptrs[w] = _dev_ptr(f, (torch.float32, torch.bfloat16), f"factor {w}")
+        dt = BF16 if f.dtype == torch.bfloat16 else F32
+        if fdt is not None and dt != fdt:
+            raise TypeError("all factors must share one dtype")
+        fdt = dt
+        if f.dim() != 2 or (R is not None and f.shape[1] != R):
+            raise ValueError("factors must be 2-D with a common rank")
+        R = f.shape[1]
+    if R is None:
+        raise ValueError("no input factor given")
+    po = _dev_ptr(out, (torch.float32,), "out")
+    if out.dim() != 2 or out.shape[1] != R:
+        raise ValueError("out must be [I_mode, R]")
+    return ptrs, fdt, R, po
 
 
 def flycoo_remap(h, next_mode: int, stream=None) -> None:

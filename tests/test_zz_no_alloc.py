@@ -1,0 +1,61 @@
+"""flycoo_spmttkrp_static_scratch: the spMTTKRP entry point that allocates
+nothing.  Its partial rows live in a fixed device array inside the library,
+for callers that must not allocate device memory at the point of the call.
+Checked through the C ABI against flycoo_spmttkrp on the same tensor, on two
+calls in a row (the array keeps the previous call's contents).  This file is
+collected last so that a stop-at-first-failure run has already run the rest.
+"""
+import numpy as np
+import pytest
+
+from synth import make_factors, random_coo
+
+from _util import rel_fro, to_np
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2309_09131_gb300 as pkg
+    pkg._native.lib()
+    return pkg
+
+
+@pytest.mark.parametrize("dims,nnz,R,dtype,g", [
+    ((400, 300, 200), 60_000, 32, torch.float32, 256),
+    ((60, 70, 50, 40), 30_000, 64, torch.bfloat16, 128),
+])
+def test_static_scratch_matches_allocated_scratch(P, dims, nnz, R, dtype, g):
+    N = len(dims)
+    idx, vals = random_coo(dims, nnz, seed=21, law="zipf", value_law="lognormal")
+    facs = [torch.from_numpy(f).cuda().to(dtype) for f in make_factors(dims, R, "normal", seed=21)]
+    T = P.FlycooTensor(idx, vals, dims, g=g, bins=48)
+    ref = T.all_modes(facs)
+    ref = [r.clone() for r in ref]
+    for call in range(2):
+        outs = [torch.full((d, R), float("nan"), device="cuda") for d in dims]
+        for n in range(N):
+            P.flycoo_spmttkrp_static_scratch(T.h, n, facs, outs[n], (n + 1) % N)
+        torch.cuda.synchronize()
+        assert T.layout_mode == 0
+        for n in range(N):
+            assert rel_fro(to_np(outs[n]), to_np(ref[n])) <= 1e-5, (call, n)
+            # same kernel, same order: the results agree bit for bit
+            assert torch.equal(outs[n], ref[n]), (call, n)
+
+
+def test_static_scratch_rejects_oversized_requests(P):
+    dims = (50, 40, 30)
+    idx, vals = random_coo(dims, 20_000, seed=3)
+    T = P.FlycooTensor(idx, vals, dims, g=1, bins=8)   # 20,000 shards per mode
+    facs = [torch.randn((d, 64), device="cuda") for d in dims]
+    out = torch.empty((50, 64), device="cuda")
+    with pytest.raises(P.FlycooError) as e:
+        P.flycoo_spmttkrp_static_scratch(T.h, 0, facs, out, 1)
+    assert e.value.status_name == "FLYCOO_ERR_INVALID_ARG"
+    assert "static scratch holds" in str(e.value)
+    assert T.layout_mode == 0
