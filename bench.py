@@ -249,7 +249,7 @@ def main(argv=None):
     Yf = [torch.from_numpy(f).cuda() for f in facs]
     outs = [torch.empty((d, R), dtype=torch.float32, device="cuda") for d in wl.dims]
     per_mode_b, step_b = step_bytes(wl.dims, wl.nnz, R, 4, elem_bytes)
-    launches_per_step = sum(1 + (1 if info["boundary_rows"][n] else 0) for n in range(N))
+    launches_per_step = sum(1 + (1 if info["fixup_super_shards"][n] else 0) for n in range(N))
 
     # ---- warm-up
     for _ in range(args.warmup):

@@ -14,9 +14,8 @@
  *  - Dense matrices are row-major.  Factor matrix Y_w is I_w x R; an output
  *    M_n is I_n x R in FP32.  Coordinates are 0-based (Section II-A).
  *  - Work is ordered on the given stream (a cudaStream_t; NULL is the legacy
- *    default stream).  Only flycoo_create, the export_* calls that fill host
- *    buffers, flycoo_cp_als_step (its scalar fit) and flycoo_timing_read wait
- *    for the stream.
+ *    default stream).  Only flycoo_create, flycoo_sync, the export_* calls
+ *    that fill host buffers and flycoo_timing_read wait for the stream.
  *  - Every entry point returns a flycoo_status and never aborts or traps;
  *    flycoo_last_error() then describes the failure (per calling thread).
  *  - A handle is not thread-safe: calls on one handle must not overlap.
@@ -54,13 +53,14 @@ typedef enum {
 
 /* Partitioning parameters (Section III-A and III-C).  Zero selects the default.
  *  m[n]  super-shard width of mode n: super-shard j holds the nonzeros whose
- *        mode-n index lies in [j*m[n], (j+1)*m[n]).  Default ceil(I_n / bins)
- *        (Eq. 1 with q = 1), so there are about `bins` super-shards per mode.
+ *        mode-n index lies in [j*m[n], (j+1)*m[n]).  At most 128: the fused
+ *        kernel keeps a super-shard's m[n] output rows in shared memory (the
+ *        cache budget of Eq. 2).  Default min(I_n, 128).
  *  g     shard size in nonzeros: each super-shard is cut into runs of g
- *        consecutive nonzeros (the last one shorter).  Default 8192, lowered
- *        to keep >= 4 shards per bin on small tensors (never below 256).
+ *        consecutive nonzeros (the last one shorter).  Default: the largest
+ *        power of two in [1024, 32768] that leaves about four shards per bin.
  *  bins  number of schedule bins of Algorithm 3, which is also the number of
- *        thread blocks of the fused kernel.  Default: 4 x the SM count. */
+ *        thread blocks of the fused kernel.  Default: 3 x the SM count. */
 typedef struct {
     uint64_t m[FLYCOO_MAX_MODES];
     uint64_t g;
@@ -78,9 +78,11 @@ typedef struct {
     uint64_t g;                                 /* shard size used                    */
     uint32_t bins;                              /* schedule bins used                 */
     uint32_t elem_bytes;                        /* bytes of one stored nonzero        */
+    uint32_t tile;                              /* layout tile, see flycoo_create     */
+    uint32_t reserved;
     uint64_t super_shards[FLYCOO_MAX_MODES];    /* k_n = ceil(I_n / m_n)              */
     uint64_t shards[FLYCOO_MAX_MODES];          /* S_n = sum_j ceil(|SS_n,j| / g)     */
-    uint64_t boundary_rows[FLYCOO_MAX_MODES];   /* rows that a shard starts or ends in */
+    uint64_t fixup_super_shards[FLYCOO_MAX_MODES]; /* super-shards without exactly one shard */
     uint64_t device_bytes;                      /* device memory the handle holds     */
 } flycoo_info;
 
@@ -89,9 +91,12 @@ typedef struct flycoo_tensor *flycoo_handle;
 /* ------------------------------------------------------------------------ */
 /* flycoo_create -- convert a COO tensor to FLYCOO (Section III-A; the       */
 /* preprocessing of Section V-J).  For every mode n it computes the layout   */
-/* L_n (nonzeros ordered by (c_n, c_{n-1}, ..., c_{n+1}, input position)),   */
-/* the super-shard and shard pointers, each nonzero's slot in L_{(n+1) mod N} */
-/* and the Algorithm 3 schedules, then stores the tensor in layout L_0.      */
+/* L_n: nonzeros ordered by their super-shard ids (ss_n, ss_{n-1}, ...,      */
+/* ss_{n+1}, input position) with ss_w = c_w div m[w], cut into super-shards */
+/* and shards, and inside each shard every run of `tile` (512) positions     */
+/* from the shard start stably re-ordered by c_n; each nonzero's slot in     */
+/* L_{(n+1) mod N}; and the Algorithm 3 schedules.  The tensor is then       */
+/* stored in layout L_0.                                                     */
 /*  N       number of modes, 3 <= N <= 5.                                    */
 /*  h_dims  N mode sizes, each in [1, 2^32 - 1].                             */
 /*  nnz     nonzeros, < 2^32 - 1.  0 is allowed.                             */
@@ -100,8 +105,8 @@ typedef struct flycoo_tensor *flycoo_handle;
 /*  d_vals  nnz float32 values.  Copied.                                     */
 /*  params  NULL or partition parameters (zeros = defaults).                 */
 /*  out     receives the handle.                                             */
-/* Errors: INVALID_ARG, INDEX_RANGE (any coordinate >= its I_w), OOM, CUDA.  */
-/* Waits for `stream`.                                                       */
+/* Errors: INVALID_ARG (also m[n] > 128), INDEX_RANGE (any coordinate >= its */
+/* I_w), OOM, CUDA.  Waits for `stream`.                                     */
 /* ------------------------------------------------------------------------ */
 flycoo_status flycoo_create(int N, const uint64_t *h_dims, uint64_t nnz, const uint32_t *d_idx,
                             const float *d_vals, const flycoo_params *params,
@@ -167,6 +172,11 @@ flycoo_status flycoo_spmttkrp_static_scratch(flycoo_handle h, int mode, const vo
 /* ------------------------------------------------------------------------ */
 flycoo_status flycoo_remap(flycoo_handle h, int next_mode, flycoo_stream_t stream);
 
+/* Wait for `stream`, then report device-side failures since the last call:  */
+/* FLYCOO_ERR_TIMEOUT if a bounded device wait (on a tile-load barrier) gave  */
+/* up; the flag is cleared.  The kernels never trap: this is how they report.  */
+flycoo_status flycoo_sync(flycoo_handle h, flycoo_stream_t stream);
+
 /* Fill *out with the handle's sizes and parameters. */
 flycoo_status flycoo_get_info(flycoo_handle h, flycoo_info *out);
 
@@ -183,11 +193,9 @@ flycoo_status flycoo_export_layout(flycoo_handle h, uint32_t *d_idx_out, float *
 /* Section III-A pointers of mode n into host buffers (any may be NULL):     */
 /*  h_ss_ptr[k_n + 1]  start of super-shard j in L_n, then nnz;              */
 /*  h_shard_ptr[S_n+1] start of each shard in L_n, then nnz;                 */
-/*  h_first_row[S_n], h_last_row[S_n]  mode-n index of the first and last   */
-/*  nonzero of each shard.                                                   */
+/*  h_shard_ss[S_n]    super-shard of each shard.                            */
 flycoo_status flycoo_export_partition(flycoo_handle h, int mode, uint64_t *h_ss_ptr,
-                                      uint64_t *h_shard_ptr, uint32_t *h_first_row,
-                                      uint32_t *h_last_row);
+                                      uint64_t *h_shard_ptr, uint32_t *h_shard_ss);
 
 /* Algorithm 3 schedules of mode n as CSR lists into host buffers:           */
 /*  which = 0: super-shards binned by shard count (the SS_List of the paper),*/

@@ -28,7 +28,7 @@ _lib = None
 
 __all__ = [
     "build", "mttkrp", "mttkrp_rows", "sampled", "layout_order", "inverse", "partition",
-    "lpt", "lpt_bins", "round_bf16", "factors_f64", "flycoo_layout", "remap",
+    "lpt", "lpt_bins", "round_bf16", "factors_f64", "tile_sort", "flycoo_layout", "remap",
 ]
 
 
@@ -52,7 +52,7 @@ def _load():
         lib.oracle_mttkrp.argtypes = [I, P, U64, P, P, P, I, I, P]
         lib.oracle_mttkrp_rows.argtypes = [I, P, U64, P, P, P, I, I, U64, P, P]
         lib.oracle_sampled.argtypes = [I, U64, P, P, I, P]
-        lib.oracle_layout_order.argtypes = [I, U64, P, I, P]
+        lib.oracle_layout_order.argtypes = [I, U64, P, P, I, P]
         lib.oracle_partition.argtypes = [U64, U64, P, U64, U64, P, P, U64, P]
         lib.oracle_lpt.argtypes = [U64, P, U64, P, P, P]
         lib.oracle_round_bf16.argtypes = [U64, P, P]
@@ -150,15 +150,17 @@ def sampled(idx, F) -> np.ndarray:
     return out
 
 
-def layout_order(idx, mode: int) -> np.ndarray:
-    """pi_n: position -> original element of layout L_n, ordered by
-    ``(c_n, c_{n-1}, ..., c_{n+1}, e)`` (Section III-B, reading stated in the
-    C source)."""
+def layout_order(idx, mode: int, m=None) -> np.ndarray:
+    """pi_n: position -> original element of layout L_n, ordered by the
+    super-shard ids ``(c_n div m_n, c_{n-1} div m_{n-1}, ..., c_{n+1} div
+    m_{n+1}, e)`` (Sections III-A/B, reading stated in the C source).  ``m``
+    defaults to all ones (order by coordinates)."""
     lib = _load()
     idx = _coo(idx)
     N, nnz = idx.shape
+    mm = np.ascontiguousarray(np.ones(N) if m is None else m, dtype=np.uint64)
     order = np.empty(nnz, dtype=np.uint32)
-    rc = lib.oracle_layout_order(N, nnz, _ptr(idx), mode, _ptr(order))
+    rc = lib.oracle_layout_order(N, nnz, _ptr(idx), _ptr(mm), mode, _ptr(order))
     if rc:
         raise ValueError(f"oracle_layout_order failed ({rc})")
     return order
@@ -223,12 +225,29 @@ def round_bf16(x: np.ndarray) -> np.ndarray:
     return out
 
 
-def flycoo_layout(idx, dims, m: Sequence[int], g: int, nbins: int) -> List[Dict[str, np.ndarray]]:
+def tile_sort(order, rows, shard_ptr, tile: int) -> np.ndarray:
+    """Stored order of a layout: inside each shard, every run of ``tile``
+    positions counted from the shard start is stably sorted by ``rows`` (the
+    output coordinate of each element).  The shard contents are unchanged."""
+    out = np.array(order, copy=True)
+    sp = np.asarray(shard_ptr, dtype=np.int64)
+    for q in range(sp.size - 1):
+        for a in range(int(sp[q]), int(sp[q + 1]), tile):
+            b = min(a + tile, int(sp[q + 1]))
+            seg = out[a:b]
+            out[a:b] = seg[np.argsort(rows[seg], kind="stable")]
+    return out
+
+
+def flycoo_layout(idx, dims, m: Sequence[int], g: int, nbins: int, tile: int = 512
+                  ) -> List[Dict[str, np.ndarray]]:
     """Everything the FLYCOO format fixes for each mode n, from the definitions:
 
-    ``order`` (pi_n), ``pos`` (its inverse: slot of each element in L_n),
-    ``ss_ptr`` and ``shard_ptr`` (Section III-A), ``first_row``/``last_row``
-    of every shard, ``next`` (slot in L_{(n+1) mod N} of the element at each
+    ``order`` (pi_n: the stored order, the super-shard key order with every
+    layout tile sorted by output coordinate), ``pos`` (its inverse: slot of
+    each element in L_n),
+    ``ss_ptr`` and ``shard_ptr`` (Section III-A), ``shard_ss`` (super-shard
+    of every shard), ``next`` (slot in L_{(n+1) mod N} of the element at each
     position of L_n: the dynamic remap of Section III-B and Algorithm 2),
     ``ss_bins`` (Algorithm 3 over super-shards, load = shard count) and
     ``shard_bins`` (Algorithm 3 over shards, load = element count).
@@ -237,21 +256,19 @@ def flycoo_layout(idx, dims, m: Sequence[int], g: int, nbins: int) -> List[Dict[
     N, nnz = idx.shape
     modes = []
     for n in range(N):
-        order = layout_order(idx, n)
-        rows_sorted = idx[n][order]
         ss_ptr, shard_ptr = partition(idx[n], int(dims[n]), int(m[n]), int(g))
-        S = shard_ptr.size - 1
+        order = tile_sort(layout_order(idx, n, m), idx[n], shard_ptr, tile)
         starts = shard_ptr[:-1].astype(np.int64)
         ends = shard_ptr[1:].astype(np.int64)
         ss_sizes = ss_ptr[1:] - ss_ptr[:-1]
         ss_shards = (ss_sizes + np.uint64(g) - np.uint64(1)) // np.uint64(g)
+        shard_ss = np.repeat(np.arange(ss_sizes.size, dtype=np.uint32), ss_shards.astype(np.int64))
         modes.append(dict(
             order=order,
             pos=inverse(order),
             ss_ptr=ss_ptr,
             shard_ptr=shard_ptr,
-            first_row=rows_sorted[starts] if S else np.zeros(0, np.uint32),
-            last_row=rows_sorted[ends - 1] if S else np.zeros(0, np.uint32),
+            shard_ss=shard_ss,
             ss_bins=lpt_bins(ss_shards, nbins)[:2],
             shard_bins=lpt_bins(ends - starts, nbins)[:2],
         ))

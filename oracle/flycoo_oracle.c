@@ -110,12 +110,18 @@ int oracle_sampled(int N, uint64_t nnz, const uint32_t *idx, const double *const
 
 /* ------------------------------------------------------------------------ */
 /* Layout L_n (Section III-B: "the tensor is ordered according to the shard  */
-/* IDs of mode n").  Reading: elements are ordered by the key                */
-/*   (c_n, c_{n-1}, c_{n-2}, ..., c_{n+1}, e)      (mode indices mod N)       */
-/* so the output index is primary and super-shards and shards are runs of    */
-/* consecutive positions.  qsort with this comparator is the definition.     */
+/* IDs of mode n"; Section III-A: every element carries its super-shard and  */
+/* shard in each mode).  Reading: with ss_w(x) = c_w(x) div m_w the          */
+/* super-shard id of x in mode w, elements are ordered by the key            */
+/*   (ss_n, ss_{n-1}, ss_{n-2}, ..., ss_{n+1}, e)      (mode indices mod N)   */
+/* so the super-shards of mode n are runs of consecutive positions, shards   */
+/* are runs of g positions inside them, and the order inside a super-shard   */
+/* follows the super-shards of the other modes.  With all m_w = 1 the key is */
+/* the coordinates themselves.  qsort with this comparator is the           */
+/* definition.                                                               */
 /* ------------------------------------------------------------------------ */
 static const uint32_t *g_idx;
+static const uint64_t *g_m;
 static uint64_t g_nnz;
 static int g_N, g_n;
 
@@ -124,19 +130,24 @@ static int cmp_layout(const void *a, const void *b)
     uint32_t ea = *(const uint32_t *)a, eb = *(const uint32_t *)b;
     for (int t = 0; t < g_N; ++t) {
         int w = ((g_n - t) % g_N + g_N) % g_N;
-        uint32_t ca = g_idx[(size_t)w * g_nnz + ea];
-        uint32_t cb = g_idx[(size_t)w * g_nnz + eb];
+        uint64_t ca = g_idx[(size_t)w * g_nnz + ea] / g_m[w];
+        uint64_t cb = g_idx[(size_t)w * g_nnz + eb] / g_m[w];
         if (ca != cb) return ca < cb ? -1 : 1;
     }
     return ea < eb ? -1 : (ea > eb ? 1 : 0);
 }
 
-/* order[p] = original COO index of the element at position p of L_n.       */
-int oracle_layout_order(int N, uint64_t nnz, const uint32_t *idx, int n, uint32_t *order)
+/* order[p] = original COO index of the element at position p of L_n;       */
+/* m[w] >= 1 is the super-shard width of mode w.                            */
+int oracle_layout_order(int N, uint64_t nnz, const uint32_t *idx, const uint64_t *m, int n,
+                        uint32_t *order)
 {
     if (N < 1 || n < 0 || n >= N || nnz > 0xffffffffull) return -1;
+    for (int w = 0; w < N; ++w)
+        if (m[w] == 0) return -1;
     for (uint64_t e = 0; e < nnz; ++e) order[e] = (uint32_t)e;
     g_idx = idx;
+    g_m = m;
     g_nnz = nnz;
     g_N = N;
     g_n = n;

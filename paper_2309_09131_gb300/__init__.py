@@ -19,6 +19,7 @@ from ._native import (  # noqa: F401
     flycoo_remap,
     flycoo_spmttkrp,
     flycoo_spmttkrp_static_scratch,
+    flycoo_sync,
     flycoo_timing_enable,
     flycoo_timing_read,
     make_params,

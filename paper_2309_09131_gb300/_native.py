@@ -42,8 +42,9 @@ class flycoo_info(ctypes.Structure):
     _fields_ = [("N", ctypes.c_int32), ("layout_mode", ctypes.c_int32), ("nnz", ctypes.c_uint64),
                 ("dims", ctypes.c_uint64 * MAX_MODES), ("m", ctypes.c_uint64 * MAX_MODES),
                 ("g", ctypes.c_uint64), ("bins", ctypes.c_uint32), ("elem_bytes", ctypes.c_uint32),
+                ("tile", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
                 ("super_shards", ctypes.c_uint64 * MAX_MODES), ("shards", ctypes.c_uint64 * MAX_MODES),
-                ("boundary_rows", ctypes.c_uint64 * MAX_MODES), ("device_bytes", ctypes.c_uint64)]
+                ("fixup_super_shards", ctypes.c_uint64 * MAX_MODES), ("device_bytes", ctypes.c_uint64)]
 
 
 _lib = None
@@ -63,9 +64,10 @@ def lib():
             "flycoo_spmttkrp": [P, I, P, I, I, P, I, P],
             "flycoo_spmttkrp_static_scratch": [P, I, P, I, I, P, I, P],
             "flycoo_remap": [P, I, P],
+            "flycoo_sync": [P, P],
             "flycoo_get_info": [P, P],
             "flycoo_export_layout": [P, P, P, P],
-            "flycoo_export_partition": [P, I, P, P, P, P],
+            "flycoo_export_partition": [P, I, P, P, P],
             "flycoo_export_schedule": [P, I, I, P, P],
             "flycoo_export_next": [P, I, P, P],
             "flycoo_timing_enable": [P, I],
@@ -202,14 +204,19 @@ def flycoo_remap(h, next_mode: int, stream=None) -> None:
     _check(lib().flycoo_remap(h, int(next_mode), _stream(stream)))
 
 
+def flycoo_sync(h, stream=None) -> None:
+    """Wait for the stream; raise FLYCOO_ERR_TIMEOUT if a bounded device wait gave up."""
+    _check(lib().flycoo_sync(h, _stream(stream)))
+
+
 def flycoo_get_info(h) -> dict:
     info = flycoo_info()
     _check(lib().flycoo_get_info(h, ctypes.byref(info)))
     N = info.N
     return dict(N=N, layout_mode=info.layout_mode, nnz=info.nnz, dims=list(info.dims[:N]),
-                m=list(info.m[:N]), g=info.g, bins=info.bins, elem_bytes=info.elem_bytes,
+                m=list(info.m[:N]), g=info.g, bins=info.bins, elem_bytes=info.elem_bytes, tile=info.tile,
                 super_shards=list(info.super_shards[:N]), shards=list(info.shards[:N]),
-                boundary_rows=list(info.boundary_rows[:N]), device_bytes=info.device_bytes)
+                fixup_super_shards=list(info.fixup_super_shards[:N]), device_bytes=info.device_bytes)
 
 
 def flycoo_export_layout(h, stream=None):
@@ -223,15 +230,14 @@ def flycoo_export_layout(h, stream=None):
 
 
 def flycoo_export_partition(h, mode: int):
+    """``(ss_ptr, shard_ptr, shard_ss)`` of ``mode`` (Section III-A)."""
     inf = flycoo_get_info(h)
     k, S = inf["super_shards"][mode], inf["shards"][mode]
     ss = np.empty(k + 1, dtype=np.uint64)
     sp = np.empty(S + 1, dtype=np.uint64)
-    fr = np.empty(S, dtype=np.uint32)
-    lr = np.empty(S, dtype=np.uint32)
-    _check(lib().flycoo_export_partition(h, int(mode), ss.ctypes.data, sp.ctypes.data, fr.ctypes.data,
-                                         lr.ctypes.data))
-    return ss, sp, fr, lr
+    sss = np.empty(S, dtype=np.uint32)
+    _check(lib().flycoo_export_partition(h, int(mode), ss.ctypes.data, sp.ctypes.data, sss.ctypes.data))
+    return ss, sp, sss
 
 
 def flycoo_export_schedule(h, mode: int, which: int):

@@ -45,6 +45,10 @@ def _stale(target: str, deps: List[str]) -> bool:
 
 
 def build(force: bool = False, verbose: bool = False, extra_flags: List[str] = ()) -> str:
+    env_flags = os.environ.get("FLYCOO_NVCC_EXTRA", "").split()
+    if env_flags:
+        extra_flags = list(extra_flags) + env_flags
+        force = True
     os.makedirs(BUILD_DIR, exist_ok=True)
     os.makedirs(LIB_DIR, exist_ok=True)
     nvcc = _nvcc()

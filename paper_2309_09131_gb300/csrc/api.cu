@@ -30,8 +30,8 @@ u64 Tensor::device_bytes() const {
     u64 b = elem[0].bytes + elem[1].bytes + partials.bytes;
     for (int n = 0; n < N; ++n) {
         const ModeMeta &m = mode[n];
-        b += m.d_shard_ptr.bytes + m.d_first_row.bytes + m.d_last_row.bytes + m.d_bin_ptr.bytes +
-             m.d_items.bytes + m.d_bnd.bytes + m.d_next.bytes;
+        b += m.d_shard_ptr.bytes + m.d_shard_ss.bytes + m.d_ss_shard_ptr.bytes + m.d_bin_ptr.bytes +
+             m.d_items.bytes + m.d_k4.bytes + m.d_next.bytes;
     }
     return b;
 }
@@ -85,71 +85,57 @@ static flycoo_status upload(DevBuf &d, const std::vector<T> &h, cudaStream_t s) 
     return FLYCOO_OK;
 }
 
-// Section III-A pointers of one mode from its row pointers, plus the shard
-// rows, both schedules and the boundary-row list of K4.
-static flycoo_status partition_mode(Tensor &t, int n, const std::vector<u32> &rp, cudaStream_t s) {
+// Section III-A pointers of one mode from its super-shard pointers, plus the
+// super-shard of every shard, both schedules and the K4 work list.
+flycoo_status partition_mode(Tensor &t, int n, const std::vector<u32> &ssp, cudaStream_t s) {
     ModeMeta &md = t.mode[n];
     const u64 I = t.dims[n];
     md.I = I;
     md.k = (I + md.m - 1) / md.m;
-    md.ss_ptr.resize(md.k + 1);
-    for (u64 j = 0; j <= md.k; ++j) md.ss_ptr[j] = rp[std::min<u64>(j * md.m, I)];
+    md.ss_ptr.assign(ssp.begin(), ssp.end());
     md.shard_ptr.clear();
+    md.shard_ss.clear();
+    md.ss_shard_ptr.assign(md.k + 1, 0);
     std::vector<u64> ss_shards(md.k);
     for (u64 j = 0; j < md.k; ++j) {
         const u64 size = md.ss_ptr[j + 1] - md.ss_ptr[j];
         ss_shards[j] = (size + t.g - 1) / t.g;
-        for (u64 q = 0; q * t.g < size; ++q) md.shard_ptr.push_back((u32)(md.ss_ptr[j] + q * t.g));
-    }
-    md.S = md.shard_ptr.size();
-    md.shard_ptr.push_back((u32)t.nnz);
-    // row of a position: rp[r] <= p < rp[r+1]
-    auto row_of = [&](u64 p) -> u32 {
-        return (u32)(std::upper_bound(rp.begin(), rp.end(), (u32)p) - rp.begin() - 1);
-    };
-    md.first_row.resize(md.S);
-    md.last_row.resize(md.S);
-    std::vector<u64> shard_size(md.S);
-    for (u64 q = 0; q < md.S; ++q) {
-        md.first_row[q] = row_of(md.shard_ptr[q]);
-        md.last_row[q] = row_of(md.shard_ptr[q + 1] - 1);
-        shard_size[q] = md.shard_ptr[q + 1] - md.shard_ptr[q];
-    }
-    lpt_schedule(ss_shards, t.bins, md.ss_bin_ptr, md.ss_items);
-    lpt_schedule(shard_size, t.bins, md.sh_bin_ptr, md.sh_items);
-    // boundary rows: distinct first/last rows of the shards with their shard range
-    md.bnd.clear();
-    for (u64 q = 0; q < md.S; ++q) {
-        const u32 rows2[2] = {md.first_row[q], md.last_row[q]};
-        for (int i = 0; i < 2; ++i) {
-            if (i == 1 && rows2[1] == rows2[0]) break;
-            const size_t nb = md.bnd.size() / 3;
-            if (nb && md.bnd[3 * (nb - 1)] == rows2[i]) md.bnd[3 * (nb - 1) + 2] = (u32)q;
-            else {
-                md.bnd.push_back(rows2[i]);
-                md.bnd.push_back((u32)q);
-                md.bnd.push_back((u32)q);
-            }
+        md.ss_shard_ptr[j] = (u32)md.shard_ptr.size();
+        for (u64 q = 0; q * t.g < size; ++q) {
+            md.shard_ptr.push_back((u32)(md.ss_ptr[j] + q * t.g));
+            md.shard_ss.push_back((u32)j);
         }
     }
+    md.S = md.shard_ptr.size();
+    md.ss_shard_ptr[md.k] = (u32)md.S;
+    md.shard_ptr.push_back((u32)t.nnz);
+    std::vector<u64> shard_size(md.S);
+    md.tile_ptr.clear();
+    for (u64 q = 0; q < md.S; ++q) {
+        shard_size[q] = md.shard_ptr[q + 1] - md.shard_ptr[q];
+        for (u64 p = md.shard_ptr[q]; p < md.shard_ptr[q + 1]; p += kLayoutTile) md.tile_ptr.push_back((u32)p);
+    }
+    md.tile_ptr.push_back((u32)t.nnz);
+    lpt_schedule(ss_shards, t.bins, md.ss_bin_ptr, md.ss_items);
+    lpt_schedule(shard_size, t.bins, md.sh_bin_ptr, md.sh_items);
+    // K4 writes the rows of every super-shard that does not have exactly one shard
+    md.k4_items.clear();
+    for (u64 j = 0; j < md.k; ++j)
+        if (ss_shards[j] != 1) md.k4_items.push_back((u32)j);
     FLY_TRY(upload(md.d_shard_ptr, md.shard_ptr, s));
-    FLY_TRY(upload(md.d_first_row, md.first_row, s));
-    FLY_TRY(upload(md.d_last_row, md.last_row, s));
+    FLY_TRY(upload(md.d_shard_ss, md.shard_ss, s));
+    FLY_TRY(upload(md.d_ss_shard_ptr, md.ss_shard_ptr, s));
     FLY_TRY(upload(md.d_bin_ptr, md.sh_bin_ptr, s));
     FLY_TRY(upload(md.d_items, md.sh_items, s));
-    FLY_TRY(upload(md.d_bnd, md.bnd, s));
+    FLY_TRY(upload(md.d_k4, md.k4_items, s));
     return FLYCOO_OK;
 }
 
 flycoo_status launch_fixup(int R, const FixupArgs &a, cudaStream_t s) {
-    if (a.nb == 0) return FLYCOO_OK;
-    const unsigned blocks = (a.nb + 7) / 8;
-    switch (R) {
-    case 16: boundary_fixup_kernel<16><<<blocks, 256, 0, s>>>(a); break;
-    case 32: boundary_fixup_kernel<32><<<blocks, 256, 0, s>>>(a); break;
-    case 64: boundary_fixup_kernel<64><<<blocks, 256, 0, s>>>(a); break;
-    default: set_error("rank %d not built", R); return FLYCOO_ERR_UNSUPPORTED;
-    }
+    if (a.nitems == 0) return FLYCOO_OK;
+    const u32 rows = std::min<u32>(a.m, a.I_out);
+    const dim3 grid(a.nitems, (rows * (u32)R + 63) / 64);
+    super_shard_fixup_kernel<<<grid, 256, 0, s>>>(a, (u32)R);
     FLY_TRY_CUDA(cudaGetLastError());
     return FLYCOO_OK;
 }
@@ -217,12 +203,13 @@ extern "C" flycoo_status flycoo_create(int N, const uint64_t *h_dims, uint64_t n
     t->N = N;
     t->nnz = nnz;
     for (int w = 0; w < N; ++w) t->dims[w] = h_dims[w];
-    t->bins = (params && params->bins) ? params->bins : (u32)(4 * t->sm_count);
+    t->bins = (params && params->bins) ? params->bins : (u32)(kBlocksPerSM * t->sm_count);
     if (params && params->g) {
         t->g = params->g;
     } else {
-        u64 g = 8192;
-        while (g > 256 && nnz / g < 4ull * t->bins) g >>= 1;
+        // about four shards per bin, a power of two in [1024, 32768]
+        u64 g = 32768;
+        while (g > 1024 && nnz / g < 4ull * t->bins) g >>= 1;
         t->g = g;
     }
     if (t->g > 0xffffffffull) {
@@ -230,18 +217,23 @@ extern "C" flycoo_status flycoo_create(int N, const uint64_t *h_dims, uint64_t n
         return FLYCOO_ERR_INVALID_ARG;
     }
     for (int w = 0; w < N; ++w) {
-        u64 m = (params && params->m[w]) ? params->m[w] : (h_dims[w] + t->bins - 1) / t->bins;
+        // a super-shard's output rows live in shared memory: at most kMaxSuperShardRows
+        u64 m = (params && params->m[w]) ? params->m[w] : std::min<u64>(h_dims[w], kMaxSuperShardRows);
+        if (m > kMaxSuperShardRows) {
+            set_error("flycoo_create: m[%d] = %llu exceeds %u rows", w, (unsigned long long)m, kMaxSuperShardRows);
+            return FLYCOO_ERR_INVALID_ARG;
+        }
         t->mode[w].m = std::max<u64>(m, 1);
+        t->max_rows = std::max<u64>(t->max_rows, t->mode[w].m);
     }
     t->elem_words = elem_words_for(N);
 
-    std::vector<std::vector<u32>> row_ptr;
-    FLY_TRY(build_flycoo(*t, d_idx, d_vals, row_ptr, s));
-    for (int n = 0; n < N; ++n) {
-        FLY_TRY(partition_mode(*t, n, row_ptr[n], s));
-        t->max_S = std::max<u64>(t->max_S, t->mode[n].S);
-    }
-    FLY_TRY(t->partials.alloc(2 * std::max<u64>(t->max_S, 1) * kMaxRank * sizeof(float)));
+    std::vector<std::vector<u32>> ss_ptr;
+    FLY_TRY(build_flycoo(*t, d_idx, d_vals, ss_ptr, s));
+    for (int n = 0; n < N; ++n) t->max_S = std::max<u64>(t->max_S, t->mode[n].S);
+    FLY_TRY(t->partials.alloc(std::max<u64>(t->max_S, 1) * t->max_rows * kMaxRank * sizeof(float)));
+    FLY_TRY(t->err.alloc(sizeof(u32)));
+    FLY_TRY_CUDA(cudaMemsetAsync(t->err.p, 0, sizeof(u32), s));
     FLY_TRY_CUDA(cudaStreamSynchronize(s));
     *out = t.release();
     return FLYCOO_OK;
@@ -324,13 +316,14 @@ extern "C" flycoo_status flycoo_spmttkrp(flycoo_handle h, int mode, const void *
     for (int q = 1; q < t.N; ++q) a.Y[q - 1] = h_factors[(mode + q) % t.N];
     a.out = d_out;
     a.shard_ptr = md.d_shard_ptr.as<u32>();
-    a.first_row = md.d_first_row.as<u32>();
-    a.last_row = md.d_last_row.as<u32>();
+    a.shard_ss = md.d_shard_ss.as<u32>();
+    a.ss_shard_ptr = md.d_ss_shard_ptr.as<u32>();
     a.bin_ptr = md.d_bin_ptr.as<u32>();
     a.bin_items = md.d_items.as<u32>();
-    a.p_head = t.partials.as<float>();
-    a.p_tail = t.partials.as<float>() + t.max_S * kMaxRank;
+    a.partials = t.partials.as<float>();
+    a.err = t.err.as<u32>();
     a.I_out = (u32)t.dims[mode];
+    a.m = (u32)md.m;
     a.S = (u32)md.S;
     a.bins = t.bins;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -344,16 +337,37 @@ extern "C" flycoo_status flycoo_spmttkrp(flycoo_handle h, int mode, const void *
         t.ev_pending.push_back({e0, e1});
     }
     FixupArgs f{};
-    f.bnd = md.d_bnd.as<u32>();
-    f.nb = (u32)(md.bnd.size() / 3);
-    f.first_row = md.d_first_row.as<u32>();
-    f.p_head = a.p_head;
-    f.p_tail = a.p_tail;
+    f.items = md.d_k4.as<u32>();
+    f.nitems = (u32)md.k4_items.size();
+    f.ss_shard_ptr = md.d_ss_shard_ptr.as<u32>();
+    f.partials = a.partials;
     f.out = d_out;
+    f.I_out = a.I_out;
+    f.m = a.m;
     FLY_TRY(launch_fixup(R, f, s));
     if (next_mode >= 0) {
         t.cur = 1 - t.cur;
         t.layout = next_mode;
+    }
+    return FLYCOO_OK;
+}
+
+extern "C" flycoo_status flycoo_sync(flycoo_handle h, flycoo_stream_t stream) {
+    clear_error();
+    if (!h) {
+        set_error("flycoo_sync: handle is NULL");
+        return FLYCOO_ERR_INVALID_ARG;
+    }
+    DeviceGuard dg(h->device);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    u32 e = 0;
+    FLY_TRY_CUDA(cudaMemcpyAsync(&e, h->err.p, sizeof(u32), cudaMemcpyDeviceToHost, s));
+    FLY_TRY_CUDA(cudaStreamSynchronize(s));
+    if (e) {
+        FLY_TRY_CUDA(cudaMemsetAsync(h->err.p, 0, sizeof(u32), s));
+        FLY_TRY_CUDA(cudaStreamSynchronize(s));
+        set_error("flycoo_sync: a bounded device wait gave up (error word 0x%x)", e);
+        return FLYCOO_ERR_TIMEOUT;
     }
     return FLYCOO_OK;
 }
@@ -389,12 +403,13 @@ extern "C" flycoo_status flycoo_get_info(flycoo_handle h, flycoo_info *out) {
     out->g = t.g;
     out->bins = t.bins;
     out->elem_bytes = (uint32_t)(t.elem_words * 4);
+    out->tile = kLayoutTile;
     for (int n = 0; n < t.N; ++n) {
         out->dims[n] = t.dims[n];
         out->m[n] = t.mode[n].m;
         out->super_shards[n] = t.mode[n].k;
         out->shards[n] = t.mode[n].S;
-        out->boundary_rows[n] = t.mode[n].bnd.size() / 3;
+        out->fixup_super_shards[n] = t.mode[n].k4_items.size();
     }
     out->device_bytes = t.device_bytes();
     return FLYCOO_OK;
@@ -413,8 +428,7 @@ extern "C" flycoo_status flycoo_export_layout(flycoo_handle h, uint32_t *d_idx_o
 }
 
 extern "C" flycoo_status flycoo_export_partition(flycoo_handle h, int mode, uint64_t *h_ss_ptr,
-                                                 uint64_t *h_shard_ptr, uint32_t *h_first_row,
-                                                 uint32_t *h_last_row) {
+                                                 uint64_t *h_shard_ptr, uint32_t *h_shard_ss) {
     clear_error();
     if (!h || mode < 0 || mode >= h->N) {
         set_error("flycoo_export_partition: bad handle or mode");
@@ -424,8 +438,7 @@ extern "C" flycoo_status flycoo_export_partition(flycoo_handle h, int mode, uint
     if (h_ss_ptr) std::copy(md.ss_ptr.begin(), md.ss_ptr.end(), h_ss_ptr);
     if (h_shard_ptr)
         for (size_t i = 0; i < md.shard_ptr.size(); ++i) h_shard_ptr[i] = md.shard_ptr[i];
-    if (h_first_row) std::copy(md.first_row.begin(), md.first_row.end(), h_first_row);
-    if (h_last_row) std::copy(md.last_row.begin(), md.last_row.end(), h_last_row);
+    if (h_shard_ss) std::copy(md.shard_ss.begin(), md.shard_ss.end(), h_shard_ss);
     return FLYCOO_OK;
 }
 

@@ -1,30 +1,43 @@
 // fused.cuh -- K2: spMTTKRP of one mode with the dynamic remap fused into the
 // same pass (Algorithm 2, one value of n), and K4: the fixed-order sum of the
-// partial rows that straddle shard boundaries.
+// row blocks of super-shards that span several shards.
 //
-// Work decomposition.  The tensor is in layout L_n: nonzeros ordered by the
-// output index c_n, in shards of at most g consecutive nonzeros (Section
-// III-A).  Thread block b walks the shards that Algorithm 3 put in bin b.
-// Inside a shard, each group of L lanes owns one contiguous slice of the
-// shard; its lanes split the rank dimension (16 bytes of every factor row per
-// lane, so a row gather is one coalesced vector load per lane).  A group
-// streams its slice in batches: the L lanes load the batch's nonzeros (and
-// their slots in L_{n+1}), store each nonzero at its slot of the next layout
-// (the fused remap), and stage the batch in shared memory.  Every lane then
-// reads each staged nonzero, gathers the N-1 input factor rows, forms
-// val * (Hadamard product) in FP32 and adds it to a running row sum held in
-// registers.  Rows are contiguous in L_n, so a row sum is complete when the
-// output index changes, unless the row touches the start or end of the slice.
+// Layout.  The tensor is in layout L_n: nonzeros ordered by super-shard id
+// ss_n = c_n div m_n, cut into shards of at most g consecutive nonzeros
+// (Section III-A).  Inside a super-shard the nonzeros are ordered by the
+// other modes' super-shard ids, so the remap to L_{n+1} is a stable scatter
+// into the k_{n+1} super-shards of the next mode (a few hundred write streams
+// rather than one per output row).
 //
-// Ownership and determinism (no atomics).  A row strictly inside one slice is
-// stored by that slice's group.  The first and last row of each slice are
-// combined with the neighbouring slices in slice order after a block barrier;
-// a row strictly inside the shard is then stored by the group whose slice it
-// starts in.  The first and last row of each shard go to a per-shard partial
-// buffer, and K4 sums those partials in shard order.  Each output row is
-// written exactly once, by exactly one thread group, and the summation order
-// depends only on the layout and the launch shape.  Rows that no nonzero
-// touches are written as zeros by whoever owns the gap before them.
+// Work decomposition.  Thread block b walks the shards that Algorithm 3 put in
+// bin b.  A shard's super-shard owns m_n output rows, which the block
+// accumulates in shared memory (the paper keeps them in cache, Eq. 2).  One
+// elected thread streams the shard's layout tiles (512 nonzeros) into a
+// double-buffered shared-memory stage with 1-D TMA bulk copies (cp.async.bulk
+// on an mbarrier), one tile ahead.  For each tile:
+//
+//  1. remap: every thread stores a few of the tile's nonzeros at their slots
+//     of L_{n+1} (Algorithm 2, the Store of the remap step), the whole tile in
+//     one burst so neighbouring slots reach L2 together;
+//  2. compute: the tile is stored sorted by row (K1 sorts every layout tile),
+//     and each group of L lanes owns a contiguous slice of it; its lanes
+//     split the rank dimension (16 bytes of a factor row per
+//     lane, one coalesced vector load per lane and row).  Per nonzero it
+//     gathers the N-1 input factor rows and adds val * Hadamard product (FP32)
+//     to a running row sum in registers; a row that ends inside the slice is
+//     added to its shared-memory accumulator;
+//  3. combine: after a block barrier, the rows that touch a slice boundary
+//     are summed over the slices in slice order and added to the accumulator.
+//
+// At the end of a shard the accumulator rows go straight to the output when
+// the super-shard has no other shard, else to the shard's row block; K4 then
+// sums the blocks of a super-shard in shard order.  Every accumulator row is
+// updated by one thread group at a time, in an order fixed by the layout and
+// the launch shape, so results are bitwise reproducible; no atomics touch the
+// data.  Rows without nonzeros come out as zeros.
+//
+// Every wait on an mbarrier is bounded; a wait that gives up sets the error
+// word and the whole block returns.
 #pragma once
 
 #include "internal.cuh"
@@ -33,20 +46,75 @@ namespace flycoo {
 
 template <int N, int R, bool BF16>
 struct FusedCfg {
-    static constexpr int VEC = BF16 ? 8 : 4;       // factor values per 16-byte load
-    static constexpr int L = R / VEC;              // lanes per group
-    static constexpr int GPW = 32 / L;             // groups per warp
+    static constexpr int VEC = BF16 ? 8 : 4;        // factor values per 16-byte load
+    static constexpr int L = R / VEC;               // lanes per group
+    static constexpr int GPW = 32 / L;              // groups per warp
     static constexpr int WARPS = 8;
     static constexpr int THREADS = WARPS * 32;
-    static constexpr int G = WARPS * GPW;          // groups per block
+    static constexpr int G = WARPS * GPW;           // groups per block
     static constexpr int EW = (N + 1 <= 4) ? 4 : 8; // 32-bit words per stored nonzero
-    static constexpr int EQ = EW / 4;              // 16-byte chunks per stored nonzero
-    static constexpr int BATCH = 8;                // nonzeros staged per group and batch
-    static constexpr int SUB = (N <= 3) ? 4 : 2;   // nonzeros whose gathers are in flight together
-    static constexpr size_t SMEM = (size_t)G * BATCH * EQ * 16 + 2 * (size_t)G * R * 4 + 3 * (size_t)G * 4;
+    static constexpr int EQ = EW / 4;               // 16-byte chunks per stored nonzero
+    static constexpr int EB = EW * 4;               // bytes per stored nonzero
+    static constexpr int SUB = (N <= 3) ? FLYCOO_SUB3 : 1; // nonzeros whose gathers are in flight together
+    static constexpr int M = (int)kMaxSuperShardRows;
+    static constexpr int CAP = (int)kLayoutTile;    // one layout tile per stage
+    // shared memory
+    static constexpr size_t STAGE = (size_t)CAP * EB + ((size_t)CAP + 8) * 4; // nonzeros + their next slots
+    static constexpr size_t ACC = (size_t)M * R * 4;                           // row accumulators
+    static constexpr size_t SUMBUF = 2 * (size_t)G * R * 4 + 3 * (size_t)G * 4; // slice summaries
+    static constexpr size_t SMEM = 2 * STAGE + ACC + SUMBUF + 64;
     static_assert(R % VEC == 0 && L >= 1 && L <= 32 && 32 % L == 0, "rank not supported");
+    static_assert(STAGE % 16 == 0 && SUMBUF % 16 == 0 && ACC % 16 == 0, "shared-memory alignment");
 };
 
+// ---------------------------------------------------------------------------
+// PTX helpers: mbarrier and 1-D TMA bulk copy (global -> shared)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ u32 smem_addr(const void *p) { return (u32)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, u32 count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, u32 bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, u32 parity) {
+    u32 ok;
+    asm volatile("{\n\t.reg .pred p;\n\t"
+                 "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(ok)
+                 : "r"(smem_addr(bar)), "r"(parity)
+                 : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ void tma_load_1d(void *dst, const void *src, u32 bytes, uint64_t *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+
+// bounded wait; true on success
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, u32 parity) {
+    for (u32 i = 0; i < kSpinLimit; ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+// ---------------------------------------------------------------------------
 template <bool BF16>
 __device__ __forceinline__ void widen(const uint4 &v, float *f) {
     if constexpr (BF16) {
@@ -84,245 +152,313 @@ __device__ __forceinline__ void load_vec(const float *src, float *v) {
 }
 
 template <int VEC>
+__device__ __forceinline__ void add_vec(float *acc, const float *src) {
+    float x[VEC];
+    load_vec<VEC>(src, x);
+#pragma unroll
+    for (int v = 0; v < VEC; ++v) acc[v] += x[v];
+}
+
+template <int VEC>
 __device__ __forceinline__ void store_zero(float *dst) {
 #pragma unroll
     for (int q = 0; q < VEC / 4; ++q) reinterpret_cast<float4 *>(dst)[q] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
+// Walks a block's sequence of tiles: the shards of its bin, each cut into tiles.
+template <int CAP>
+struct TileCursor {
+    u32 it, it_end, s, start, len, shard_end;
+    __device__ void load_shard(const FusedArgs &a) {
+        s = a.bin_items[it];
+        start = a.shard_ptr[s];
+        shard_end = a.shard_ptr[s + 1];
+        len = min((u32)CAP, shard_end - start);
+    }
+    __device__ void begin(const FusedArgs &a, u32 b) {
+        it = a.bin_ptr[b];
+        it_end = a.bin_ptr[b + 1];
+        if (it < it_end) load_shard(a);
+    }
+    __device__ bool valid() const { return it < it_end; }
+    __device__ bool first_tile(const FusedArgs &a) const { return start == a.shard_ptr[s]; }
+    __device__ bool last_tile() const { return start + len == shard_end; }
+    __device__ void advance(const FusedArgs &a) {
+        if (start + len < shard_end) {
+            start += len;
+            len = min((u32)CAP, shard_end - start);
+        } else if (++it < it_end) {
+            load_shard(a);
+        }
+    }
+};
+
 template <int N, int R, bool BF16>
-__global__ void __launch_bounds__(256) fused_mttkrp_remap_kernel(const FusedArgs a) {
+__global__ void __launch_bounds__(256, kBlocksPerSM) fused_mttkrp_remap_kernel(const FusedArgs a) {
     using C = FusedCfg<N, R, BF16>;
     constexpr int VEC = C::VEC;
     constexpr int RV = R / VEC; // 16-byte chunks per factor row
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    uint4 *stage = reinterpret_cast<uint4 *>(smem_raw);
-    float *hacc = reinterpret_cast<float *>(stage + C::G * C::BATCH * C::EQ);
-    float *tacc = hacc + C::G * R;
-    u32 *hrow = reinterpret_cast<u32 *>(tacc + C::G * R);
-    u32 *trow = hrow + C::G;
-    u32 *multi = trow + C::G;
+    constexpr int CAP = C::CAP;
+    constexpr int G = C::G;
+    constexpr int M = C::M;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    float *acc = reinterpret_cast<float *>(smem_raw + 2 * C::STAGE);          // [M][R]
+    float *hacc = acc + M * R;                                               // [G][R]
+    float *tacc = hacc + G * R;                                              // [G][R]
+    u32 *hrow = reinterpret_cast<u32 *>(tacc + G * R);                       // [G]
+    u32 *trow = hrow + G;
+    u32 *multi = trow + G;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw + 2 * C::STAGE + C::ACC + C::SUMBUF);
 
-    const int lane = threadIdx.x & 31;
-    const int warp = threadIdx.x >> 5;
+    const int tid = threadIdx.x;
+    const int lane = tid & 31;
+    const int warp = tid >> 5;
     const int k = lane % C::L;
     const int grp = warp * C::GPW + lane / C::L;
     const bool remap = a.elem_out != nullptr;
     const uint4 *__restrict__ ein = static_cast<const uint4 *>(a.elem_in);
     uint4 *__restrict__ eout = static_cast<uint4 *>(a.elem_out);
-    const u32 *__restrict__ next = a.next;
-    float *__restrict__ out = a.out;
     const uint4 *Yp[N - 1];
 #pragma unroll
     for (int t = 0; t < N - 1; ++t) Yp[t] = static_cast<const uint4 *>(a.Y[t]) + k;
-    uint4 *my_stage = stage + grp * C::BATCH * C::EQ;
     float *my_hacc = hacc + grp * R + k * VEC;
     float *my_tacc = tacc + grp * R + k * VEC;
 
-    const u32 it_end = a.bin_ptr[blockIdx.x + 1];
-    for (u32 it = a.bin_ptr[blockIdx.x]; it < it_end; ++it) {
-        const u32 s = a.bin_items[it];
-        const u32 start = a.shard_ptr[s];
-        const u32 len = a.shard_ptr[s + 1] - start;
-        const u32 chunk = (len + C::G - 1) / C::G;
-        const u32 geff = (len + chunk - 1) / chunk;
-        const u32 lo = start + min((u32)grp * chunk, len);
-        const u32 hi = start + min((u32)(grp + 1) * chunk, len);
-        const u32 first_row = a.first_row[s];
-        const u32 last_row = a.last_row[s];
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
 
-        // empty rows before this shard (and after the last shard)
-        {
-            const u32 z0 = (s == 0) ? 0u : a.last_row[s - 1] + 1u;
-            for (u32 r = z0 + grp; r < first_row; r += C::G) store_zero<VEC>(out + (size_t)r * R + k * VEC);
-            if (s + 1 == a.S)
-                for (u32 r = last_row + 1u + grp; r < a.I_out; r += C::G)
-                    store_zero<VEC>(out + (size_t)r * R + k * VEC);
-        }
+    TileCursor<CAP> cur, pre;
+    cur.begin(a, blockIdx.x);
+    pre = cur;
+    auto issue = [&](int st, const TileCursor<CAP> &c) {
+        unsigned char *sb = smem_raw + (size_t)st * C::STAGE;
+        const u32 nlo = c.start & ~3u;
+        const u32 nhi = (c.start + c.len + 3u) & ~3u;
+        u32 bytes = c.len * C::EB;
+        if (remap) bytes += (nhi - nlo) * 4u;
+        fence_proxy_async_smem();
+        mbar_arrive_expect_tx(&bar[st], bytes);
+        tma_load_1d(sb, ein + (size_t)c.start * C::EQ, c.len * C::EB, &bar[st]);
+        if (remap) tma_load_1d(sb + (size_t)CAP * C::EB, a.next + nlo, (nhi - nlo) * 4u, &bar[st]);
+    };
+    if (tid == 0 && pre.valid()) {
+        issue(0, pre);
+        pre.advance(a);
+        if (pre.valid()) issue(1, pre);
+    }
 
-        float acc[VEC];
-#pragma unroll
-        for (int v = 0; v < VEC; ++v) acc[v] = 0.f;
-        u32 cur = kInvalidRow;
-        bool first = true;
+    for (u32 q = 0; cur.valid(); ++q) {
+        const int st = q & 1;
+        const u32 s = cur.s;
+        const u32 tstart = cur.start;
+        const u32 tlen = cur.len;
+        const bool first_tile = cur.first_tile(a);
+        const bool last_tile = cur.last_tile();
+        const u32 j = a.shard_ss[s];
+        const u32 row_base = j * a.m;
+        const u32 m_eff = min(a.m, a.I_out - row_base);
+        const unsigned char *sb = smem_raw + (size_t)st * C::STAGE;
+        const uint4 *selem = reinterpret_cast<const uint4 *>(sb);
+        const u32 *snext = reinterpret_cast<const u32 *>(sb + (size_t)CAP * C::EB) + (tstart & 3u);
 
-        for (u32 b0 = 0; b0 < chunk; b0 += C::BATCH) {
-            // stage the batch; the fused remap stores each nonzero at its next slot
-            for (int j = k; j < C::BATCH; j += C::L) {
-                const u32 p = lo + b0 + j;
-                uint4 e[C::EQ];
-                if (p < hi) {
+        if (first_tile)
+            for (u32 i = tid; i < m_eff * (R / 4); i += C::THREADS)
+                reinterpret_cast<float4 *>(acc)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+
+        // warp-uniform, so the warp-collective sort below runs with every lane or none
+        const bool timed_out = __any_sync(0xffffffffu, !mbar_wait_bounded(&bar[st], (q >> 1) & 1u));
+
+        // 1. remap burst
+        if (remap && !timed_out) {
+            for (u32 i = tid; i < tlen; i += C::THREADS) {
+                u32 w[C::EW], r[C::EW];
 #pragma unroll
-                    for (int q = 0; q < C::EQ; ++q) e[q] = __ldcs(ein + (size_t)p * C::EQ + q);
-                    if (remap) {
-                        const u32 d = __ldcs(next + p);
-                        u32 w[C::EW], r[C::EW];
-#pragma unroll
-                        for (int q = 0; q < C::EQ; ++q) {
-                            w[4 * q] = e[q].x;
-                            w[4 * q + 1] = e[q].y;
-                            w[4 * q + 2] = e[q].z;
-                            w[4 * q + 3] = e[q].w;
-                        }
-#pragma unroll
-                        for (int t = 0; t < C::EW; ++t) r[t] = (t < N) ? w[(t + 1) % N] : w[t];
-#pragma unroll
-                        for (int q = 0; q < C::EQ; ++q)
-                            eout[(size_t)d * C::EQ + q] = make_uint4(r[4 * q], r[4 * q + 1], r[4 * q + 2], r[4 * q + 3]);
-                    }
-                } else {
-#pragma unroll
-                    for (int q = 0; q < C::EQ; ++q) e[q] = make_uint4(0u, 0u, 0u, 0u);
+                for (int c = 0; c < C::EQ; ++c) {
+                    const uint4 x = selem[i * C::EQ + c];
+                    w[4 * c] = x.x;
+                    w[4 * c + 1] = x.y;
+                    w[4 * c + 2] = x.z;
+                    w[4 * c + 3] = x.w;
                 }
 #pragma unroll
-                for (int q = 0; q < C::EQ; ++q) my_stage[j * C::EQ + q] = e[q];
-            }
-            __syncwarp();
+                for (int t = 0; t < C::EW; ++t) r[t] = (t < N) ? w[(t + 1) % N] : w[t];
+                const size_t d = snext[i];
 #pragma unroll
-            for (int j0 = 0; j0 < C::BATCH; j0 += C::SUB) {
+                for (int c = 0; c < C::EQ; ++c)
+                    eout[d * C::EQ + c] = make_uint4(r[4 * c], r[4 * c + 1], r[4 * c + 2], r[4 * c + 3]);
+            }
+        }
+
+        // 2. compute this group's slice of the tile (stored sorted by row).  An odd
+        // slice length keeps the groups of a warp on different shared-memory banks.
+        u32 chunk = (tlen + G - 1) / G;
+        chunk |= 1u;
+        const u32 geff = (tlen + chunk - 1) / chunk;
+        const u32 lo = min((u32)grp * chunk, tlen);
+        const u32 hi = min((u32)(grp + 1) * chunk, tlen);
+        float racc[VEC];
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) racc[v] = 0.f;
+        u32 crow = kInvalidRow;
+        bool first = true;
+        if (!timed_out) {
+            for (u32 j0 = 0; j0 < chunk; j0 += C::SUB) {
                 uint4 raw[C::SUB][N - 1];
                 u32 row[C::SUB];
                 float val[C::SUB];
 #pragma unroll
-                for (int j = 0; j < C::SUB; ++j) {
+                for (int u = 0; u < C::SUB; ++u) {
+                    const u32 p = lo + j0 + u;
+                    const bool v = p < hi;
+                    // position 0 always exists (tlen >= 1): a stand-in for out-of-slice slots
+                    const u32 e = v ? p : 0u;
                     u32 w[C::EW];
 #pragma unroll
-                    for (int q = 0; q < C::EQ; ++q) {
-                        const uint4 x = my_stage[(j0 + j) * C::EQ + q];
-                        w[4 * q] = x.x;
-                        w[4 * q + 1] = x.y;
-                        w[4 * q + 2] = x.z;
-                        w[4 * q + 3] = x.w;
+                    for (int c = 0; c < C::EQ; ++c) {
+                        const uint4 x = selem[e * C::EQ + c];
+                        w[4 * c] = x.x;
+                        w[4 * c + 1] = x.y;
+                        w[4 * c + 2] = x.z;
+                        w[4 * c + 3] = x.w;
                     }
-                    row[j] = w[0];
-                    val[j] = __uint_as_float(w[N]);
+                    row[u] = v ? min(w[0] - row_base, (u32)M - 1u) : kInvalidRow;
+                    val[u] = __uint_as_float(w[N]);
 #pragma unroll
-                    for (int t = 1; t < N; ++t) raw[j][t - 1] = __ldg(Yp[t - 1] + (size_t)w[t] * RV);
+                    for (int t = 1; t < N; ++t) raw[u][t - 1] = __ldg(Yp[t - 1] + (size_t)w[t] * RV);
                 }
 #pragma unroll
-                for (int j = 0; j < C::SUB; ++j) {
-                    if (lo + b0 + j0 + j < hi) {
-                        float prod[VEC];
-                        widen<BF16>(raw[j][0], prod);
+                for (int u = 0; u < C::SUB; ++u) {
+                    if (row[u] == kInvalidRow) continue;
+                    float prod[VEC];
+                    widen<BF16>(raw[u][0], prod);
 #pragma unroll
-                        for (int t = 1; t < N - 1; ++t) {
-                            float f[VEC];
-                            widen<BF16>(raw[j][t], f);
+                    for (int t = 1; t < N - 1; ++t) {
+                        float f[VEC];
+                        widen<BF16>(raw[u][t], f);
 #pragma unroll
-                            for (int v = 0; v < VEC; ++v) prod[v] *= f[v];
-                        }
-                        if (row[j] != cur) {
-                            if (cur != kInvalidRow) {
-                                if (first) {
-                                    store_vec<VEC>(my_hacc, acc);
-                                    if (k == 0) hrow[grp] = cur;
-                                    first = false;
-                                } else {
-                                    store_vec<VEC>(out + (size_t)cur * R + k * VEC, acc);
-                                }
-                                for (u32 r = cur + 1u; r < row[j]; ++r)
-                                    store_zero<VEC>(out + (size_t)r * R + k * VEC);
-                            }
-                            cur = row[j];
-#pragma unroll
-                            for (int v = 0; v < VEC; ++v) acc[v] = 0.f;
-                        }
-#pragma unroll
-                        for (int v = 0; v < VEC; ++v) acc[v] = fmaf(val[j], prod[v], acc[v]);
+                        for (int v = 0; v < VEC; ++v) prod[v] *= f[v];
                     }
+                    if (row[u] != crow) {
+                        if (crow != kInvalidRow) {
+                            if (first) {
+                                store_vec<VEC>(my_hacc, racc);
+                                if (k == 0) hrow[grp] = crow;
+                                first = false;
+                            } else {
+                                // a row that starts and ends inside this slice: only this group holds it
+                                float *dst = acc + crow * R + k * VEC;
+                                add_vec<VEC>(racc, dst);
+                                store_vec<VEC>(dst, racc);
+                            }
+                        }
+                        crow = row[u];
+#pragma unroll
+                        for (int v = 0; v < VEC; ++v) racc[v] = 0.f;
+                    }
+#pragma unroll
+                    for (int v = 0; v < VEC; ++v) racc[v] = fmaf(val[u], prod[v], racc[v]);
                 }
             }
-            __syncwarp();
         }
-
-        // slice summary: a single run goes to the head slot, else the last run to the tail slot
+        // slice summary: a single run in the head slot, else the last run in the tail slot
         if ((u32)grp < geff) {
             if (first) {
-                store_vec<VEC>(my_hacc, acc);
+                store_vec<VEC>(my_hacc, racc);
                 if (k == 0) {
-                    hrow[grp] = cur;
+                    hrow[grp] = crow;
                     multi[grp] = 0u;
                 }
             } else {
-                store_vec<VEC>(my_tacc, acc);
+                store_vec<VEC>(my_tacc, racc);
                 if (k == 0) {
-                    trow[grp] = cur;
+                    trow[grp] = crow;
                     multi[grp] = 1u;
                 }
             }
         }
-        __syncthreads();
+        if (__syncthreads_or(timed_out)) {
+            if (tid == 0) atomicOr(a.err, 1u);
+            return;
+        }
+        // every thread is past its reads of this stage: load the tile after next into it
+        if (tid == 0) {
+            pre.advance(a);
+            if (pre.valid()) issue(st, pre);
+        }
 
+        // 3. runs that touch a slice boundary: summed in slice order by the group
+        // where they start, then added to the accumulator
         if ((u32)grp < geff) {
+            auto extend = [&](u32 r, float *sum) {
+                for (u32 g2 = grp + 1; g2 < geff; ++g2) {
+                    if (hrow[g2] != r) return;
+                    add_vec<VEC>(sum, hacc + g2 * R + k * VEC);
+                    if (multi[g2]) return;
+                }
+            };
             const u32 h = hrow[grp];
             const bool mg = multi[grp] != 0u;
             const u32 prev_last = (grp == 0) ? kInvalidRow : (multi[grp - 1] ? trow[grp - 1] : hrow[grp - 1]);
-            // sum a run that starts in this slice over the following slices, in order;
-            // returns true if it reaches the end of the shard
-            auto extend = [&](u32 r, float *sum) -> bool {
-                for (u32 q = grp + 1; q < geff; ++q) {
-                    if (hrow[q] != r) return false;
-                    float x[VEC];
-                    load_vec<VEC>(hacc + q * R + k * VEC, x);
-#pragma unroll
-                    for (int v = 0; v < VEC; ++v) sum[v] += x[v];
-                    if (multi[q]) return false;
-                }
-                return true;
-            };
-            auto emit = [&](u32 r, const float *sum, bool is_start, bool reach_end) {
-                if (is_start) store_vec<VEC>(a.p_head + (size_t)s * R + k * VEC, sum);
-                else if (reach_end) store_vec<VEC>(a.p_tail + (size_t)s * R + k * VEC, sum);
-                else store_vec<VEC>(out + (size_t)r * R + k * VEC, sum);
-            };
             if (grp == 0 || prev_last != h) {
                 float sum[VEC];
                 load_vec<VEC>(my_hacc, sum);
-                const bool reach_end = mg ? false : extend(h, sum);
-                emit(h, sum, grp == 0, reach_end);
+                if (!mg) extend(h, sum);
+                float *dst = acc + h * R + k * VEC;
+                add_vec<VEC>(sum, dst);
+                store_vec<VEC>(dst, sum);
             }
             if (mg) {
                 const u32 tr = trow[grp];
                 float sum[VEC];
                 load_vec<VEC>(my_tacc, sum);
-                const bool reach_end = extend(tr, sum);
-                emit(tr, sum, false, reach_end);
+                extend(tr, sum);
+                float *dst = acc + tr * R + k * VEC;
+                add_vec<VEC>(sum, dst);
+                store_vec<VEC>(dst, sum);
             }
-            if (grp > 0)
-                for (u32 r = prev_last + 1u; r < h; ++r) store_zero<VEC>(out + (size_t)r * R + k * VEC);
         }
+
+        // the next tile's slices may hold any of these rows: their adds wait here
         __syncthreads();
+        // end of the shard: its super-shard's rows to the output, or to the shard's row block
+        if (last_tile) {
+            const bool alone = a.ss_shard_ptr[j + 1] - a.ss_shard_ptr[j] == 1u;
+            float4 *dst = alone ? reinterpret_cast<float4 *>(a.out + (size_t)row_base * R)
+                                : reinterpret_cast<float4 *>(a.partials + (size_t)s * a.m * R);
+            for (u32 i = tid; i < m_eff * (R / 4); i += C::THREADS) dst[i] = reinterpret_cast<const float4 *>(acc)[i];
+            __syncthreads();
+        }
+        cur.advance(a);
     }
 }
 
-// K4: one warp per boundary row; sums the shard partials in shard order.
-template <int R>
-__global__ void __launch_bounds__(256) boundary_fixup_kernel(const FixupArgs a) {
-    constexpr int PER = (R + 31) / 32;
-    const u32 w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (w >= a.nb) return;
-    const u32 row = a.bnd[3 * (size_t)w];
-    const u32 s_lo = a.bnd[3 * (size_t)w + 1];
-    const u32 s_hi = a.bnd[3 * (size_t)w + 2];
-    const float *first = (a.first_row[s_lo] == row) ? a.p_head : a.p_tail;
-    float sum[PER];
-#pragma unroll
-    for (int i = 0; i < PER; ++i) {
-        const int r = lane + 32 * i;
-        sum[i] = (r < R) ? first[(size_t)s_lo * R + r] : 0.f;
-    }
-#pragma unroll 4
-    for (u32 s = s_lo + 1; s <= s_hi; ++s) {
-#pragma unroll
-        for (int i = 0; i < PER; ++i) {
-            const int r = lane + 32 * i;
-            if (r < R) sum[i] += a.p_head[(size_t)s * R + r];
-        }
-    }
-#pragma unroll
-    for (int i = 0; i < PER; ++i) {
-        const int r = lane + 32 * i;
-        if (r < R) a.out[(size_t)row * R + r] = sum[i];
+// K4: rows of the super-shards that do not have exactly one shard: the sum of
+// their shards' row blocks in shard order (zero for an empty super-shard).
+// Block (item, c) covers 64 consecutive floats of the super-shard's rows; its
+// four 64-thread parts take every fourth shard and are added in part order.
+static __global__ void __launch_bounds__(256) super_shard_fixup_kernel(const FixupArgs a, u32 R) {
+    __shared__ float part_sum[4][64];
+    const u32 item = blockIdx.x;
+    const u32 j = a.items[item];
+    const u32 row_base = j * a.m;
+    const u32 m_eff = min(a.m, a.I_out - row_base);
+    const u32 nfl = m_eff * R;
+    const u32 f = blockIdx.y * 64 + (threadIdx.x & 63);
+    const u32 part = threadIdx.x >> 6;
+    const u32 s0 = a.ss_shard_ptr[j], s1 = a.ss_shard_ptr[j + 1];
+    float sum = 0.f;
+    if (f < nfl)
+        for (u32 s = s0 + part; s < s1; s += 4) sum += a.partials[(size_t)s * a.m * R + f];
+    part_sum[part][threadIdx.x & 63] = sum;
+    __syncthreads();
+    if (threadIdx.x < 64 && f < nfl) {
+        const float t = ((part_sum[0][threadIdx.x] + part_sum[1][threadIdx.x]) + part_sum[2][threadIdx.x]) +
+                        part_sum[3][threadIdx.x];
+        a.out[(size_t)row_base * R + f] = t;
     }
 }
 

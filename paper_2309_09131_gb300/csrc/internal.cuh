@@ -70,13 +70,15 @@ struct DevBuf {
 // --------------------------------------------------------------------------
 struct ModeMeta {
     u64 I = 0, m = 0, k = 0, S = 0;
-    std::vector<u64> ss_ptr;              // k + 1
-    std::vector<u32> shard_ptr;           // S + 1
-    std::vector<u32> first_row, last_row; // S
+    std::vector<u64> ss_ptr;              // k + 1: first position of each super-shard in L_n
+    std::vector<u32> shard_ptr;           // S + 1: first position of each shard in L_n
+    std::vector<u32> shard_ss;            // S: super-shard of each shard
+    std::vector<u32> ss_shard_ptr;        // k + 1: shards of super-shard j are [ss_shard_ptr[j], ss_shard_ptr[j+1])
     std::vector<u32> ss_bin_ptr, ss_items;  // Algorithm 3 over super-shards
     std::vector<u32> sh_bin_ptr, sh_items;  // Algorithm 3 over shards (kernel schedule)
-    std::vector<u32> bnd;                   // boundary rows: (row, s_lo, s_hi) triples
-    DevBuf d_shard_ptr, d_first_row, d_last_row, d_bin_ptr, d_items, d_bnd, d_next;
+    std::vector<u32> k4_items;              // super-shards whose rows K4 writes (not exactly one shard)
+    std::vector<u32> tile_ptr;              // T + 1: layout tiles (K1 only)
+    DevBuf d_shard_ptr, d_shard_ss, d_ss_shard_ptr, d_bin_ptr, d_items, d_k4, d_next;
 };
 
 struct Tensor {
@@ -92,7 +94,9 @@ struct Tensor {
     int cur = 0;        // which element buffer holds the current layout
     u64 max_S = 0;
     DevBuf elem[2];
-    DevBuf partials;    // 2 x max_S x kMaxRank floats (head then tail)
+    u64 max_rows = 0;   // max over modes of min(m_n, I_n): rows of a super-shard
+    DevBuf partials;    // max_S x max_rows x kMaxRank floats: one row block per shard
+    DevBuf err;         // device error word: bit 0 = a bounded device wait gave up
     ModeMeta mode[FLYCOO_MAX_MODES];
     // kernel timing
     bool timing = false;
@@ -103,7 +107,28 @@ struct Tensor {
 };
 
 constexpr int kMaxRank = 64;
+// largest super-shard width m_n: the fused kernel keeps a super-shard's output
+// rows (m_n x R FP32) in shared memory
+constexpr u32 kMaxSuperShardRows = 128;
+// layout tile: inside a shard, each run of kLayoutTile positions (counted from
+// the shard start) is stored sorted by output index; the fused kernel works
+// tile by tile
+constexpr u32 kLayoutTile = 512;
 constexpr u32 kInvalidRow = 0xffffffffu;
+// iteration limit of every device-side wait (mbarrier polls); ~0.1-1 s
+constexpr u32 kSpinLimit = 1u << 24;
+
+// resident blocks per SM the fused kernel is built for (registers and shared
+// memory are sized for it); the default number of schedule bins is this
+// times the SM count, so one launch is one wave
+#ifndef FLYCOO_BLOCKS_PER_SM
+#define FLYCOO_BLOCKS_PER_SM 3
+#endif
+constexpr int kBlocksPerSM = FLYCOO_BLOCKS_PER_SM;
+// nonzeros of a 3-mode tensor whose factor-row gathers are issued together
+#ifndef FLYCOO_SUB3
+#define FLYCOO_SUB3 2
+#endif
 
 inline int elem_words_for(int N) { return (N + 1 <= 4) ? 4 : 8; }
 
@@ -114,9 +139,12 @@ inline int elem_words_for(int N) { return (N + 1 <= 4) ? 4 : 8; }
 u64 scan_scratch_words(u64 n);
 flycoo_status exclusive_scan_u32(const u32 *in, u32 *out, u64 n, u32 *scratch, cudaStream_t s);
 
-// K1: layouts, remap permutations, row pointers and the L_0 element buffer
+// K1: layouts, remap permutations, super-shard pointers and the L_0 element buffer
 flycoo_status build_flycoo(Tensor &t, const u32 *d_idx, const float *d_vals,
-                           std::vector<std::vector<u32>> &row_ptr_host, cudaStream_t s);
+                           std::vector<std::vector<u32>> &ss_ptr_host, cudaStream_t s);
+
+// host bookkeeping of one mode from its super-shard pointers (api.cu)
+flycoo_status partition_mode(Tensor &t, int n, const std::vector<u32> &ssp, cudaStream_t s);
 
 // standalone remap step L_n -> L_{n+1} (and layout export)
 flycoo_status launch_remap_step(const Tensor &t, int n, const void *in, void *out, cudaStream_t s);
@@ -132,20 +160,26 @@ struct FusedArgs {
     const u32 *next;           // nullptr: no remap
     const void *Y[FLYCOO_MAX_MODES - 1]; // factors of slots 1..N-1 of the current layout
     float *out;
-    const u32 *shard_ptr, *first_row, *last_row;
+    const u32 *shard_ptr;      // S + 1
+    const u32 *shard_ss;       // S
+    const u32 *ss_shard_ptr;   // k + 1
     const u32 *bin_ptr, *bin_items;
-    float *p_head, *p_tail;    // S x R each
+    float *partials;           // row block of shard s at s * m * R
+    u32 *err;                  // device error word
     u32 I_out;
+    u32 m;                     // super-shard width of the output mode
     u32 S;
     u32 bins;
 };
 
 struct FixupArgs {
-    const u32 *bnd;    // triples (row, s_lo, s_hi)
-    u32 nb;
-    const u32 *first_row;
-    const float *p_head, *p_tail;
+    const u32 *items;          // super-shards K4 writes
+    u32 nitems;
+    const u32 *ss_shard_ptr;
+    const float *partials;
     float *out;
+    u32 I_out;
+    u32 m;
 };
 
 flycoo_status launch_fused(int N, int R, flycoo_dtype dt, const FusedArgs &a, cudaStream_t s);

@@ -1,11 +1,14 @@
 // partition.cu -- K1: FLYCOO preprocessing on the GPU (Section III-A; the
 // preprocessing stages of Section V-J) plus the standalone remap step.
 //
-// The layout L_n orders the nonzeros by (c_n, c_{n-1}, ..., c_{n+1}, input
-// position).  Under this cyclic key, L_{n+1} is exactly L_n stably sorted by
-// c_{n+1} alone, and L_0 is the input order stably sorted by c_1, c_2, ...,
-// c_{N-1} and finally c_0.  K1 therefore runs 2N-1 stable sorts, each a few
-// 8-bit LSD radix passes (histogram, exclusive scan, stable scatter).  Every
+// The layout L_n orders the nonzeros by their super-shard ids
+// (ss_n, ss_{n-1}, ..., ss_{n+1}, input position), ss_w = c_w div m_w.  Under
+// this cyclic key, L_{n+1} is exactly L_n stably sorted by ss_{n+1} alone, and
+// L_0 is the input order stably sorted by ss_1, ss_2, ..., ss_{N-1} and
+// finally ss_0.  K1 therefore runs 2N-1 stable sorts, each a few 8-bit LSD
+// radix passes (histogram, exclusive scan, stable scatter).  The stored order
+// then sorts every layout tile (kLayoutTile positions of a shard) by output
+// index, stably, so the fused kernel finds each row of a tile contiguous.  Every
 // step is integer work with no atomics on the data path, so the layouts,
 // pointers and remap permutations are bit-exact and deterministic.  There is
 // no spin-wait anywhere: the scan is a plain reduce-then-scan.
@@ -243,12 +246,18 @@ __global__ void gather_kernel(const u32 *src, const u32 *perm, u32 *dst, u64 n) 
         dst[i] = src[perm[i]];
 }
 
+// super-shard id of each element of a permuted order: dst[i] = src[perm[i]] / m
+__global__ void gather_div_kernel(const u32 *src, const u32 *perm, u32 *dst, u64 n, u32 m) {
+    for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (u64)gridDim.x * blockDim.x)
+        dst[i] = src[perm[i]] / m;
+}
+
 __global__ void inverse_kernel(const u32 *perm, u32 *inv, u64 n) {
     for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (u64)gridDim.x * blockDim.x)
         inv[perm[i]] = (u32)i;
 }
 
-// row_ptr[r] = first position whose row is >= r (rows sorted ascending), r in [0, I]
+// ptr[r] = first position whose key is >= r (keys sorted ascending), r in [0, I]
 __global__ void row_ptr_kernel(const u32 *rows, u64 n, u64 I, u32 *row_ptr) {
     for (u64 p = (u64)blockIdx.x * blockDim.x + threadIdx.x; p <= n; p += (u64)gridDim.x * blockDim.x) {
         const int64_t prev = (p == 0) ? -1 : (int64_t)rows[p - 1];
@@ -306,6 +315,72 @@ __global__ void export_layout_kernel(const u32 *elem, int ew, int N, int layout,
     }
 }
 
+// Layout tiles: inside every shard, runs of kLayoutTile positions (from the
+// shard start) are stored sorted by output index (stable).  One block per
+// tile: per-warp row counts, a scan, then stable ranks from __match_any_sync.
+__global__ void __launch_bounds__(256)
+    tile_sort_kernel(const u32 *pi_in, u32 *pi_out, const u32 *tile_ptr, const u32 *coord, u32 m) {
+    constexpr int W = 8;
+    constexpr int M = (int)kMaxSuperShardRows;
+    __shared__ u32 cnt[W][M];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const u32 start = tile_ptr[blockIdx.x];
+    const u32 len = tile_ptr[blockIdx.x + 1] - start;
+    for (int i = threadIdx.x; i < W * M; i += blockDim.x) (&cnt[0][0])[i] = 0u;
+    const u32 row_base = (coord[pi_in[start]] / m) * m;
+    __syncthreads();
+    const u32 per = (len + W - 1) / W;
+    const u32 lo = min((u32)warp * per, len), hi = min(lo + per, len);
+    const unsigned lt = (1u << lane) - 1u;
+    for (u32 b0 = lo; b0 < hi; b0 += 32) {
+        const u32 i = b0 + lane;
+        const bool v = i < hi;
+        const u32 lr = v ? min(coord[pi_in[start + i]] - row_base, (u32)M - 1u) : 0x10000u + lane;
+        const unsigned peers = __match_any_sync(0xffffffffu, lr);
+        if (v && (peers & lt) == 0) cnt[warp][lr] += __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    if (warp == 0) {
+        u32 tot[4], run = 0;
+        for (int c = 0; c < 4; ++c) {
+            u32 t = 0;
+            for (int w = 0; w < W; ++w) t += cnt[w][lane * 4 + c];
+            tot[c] = t;
+            run += t;
+        }
+        u32 incl = run;
+        for (int d = 1; d < 32; d <<= 1) {
+            const u32 y = __shfl_up_sync(0xffffffffu, incl, d);
+            if (lane >= d) incl += y;
+        }
+        u32 base = incl - run;
+        for (int c = 0; c < 4; ++c) {
+            u32 o = base;
+            for (int w = 0; w < W; ++w) {
+                const u32 x = cnt[w][lane * 4 + c];
+                cnt[w][lane * 4 + c] = o;
+                o += x;
+            }
+            base += tot[c];
+        }
+    }
+    __syncthreads();
+    for (u32 b0 = lo; b0 < hi; b0 += 32) {
+        const u32 i = b0 + lane;
+        const bool v = i < hi;
+        const u32 e = v ? pi_in[start + i] : 0u;
+        const u32 lr = v ? min(coord[e] - row_base, (u32)M - 1u) : 0x10000u + lane;
+        const unsigned peers = __match_any_sync(0xffffffffu, lr);
+        u32 pos = 0;
+        if (v) pos = cnt[warp][lr] + __popc(peers & lt);
+        __syncwarp();
+        if (v && (peers & lt) == 0) cnt[warp][lr] += __popc(peers);
+        __syncwarp();
+        if (v && pos < len) pi_out[start + pos] = e;
+    }
+}
+
 inline unsigned grid_for(u64 n, int threads = 256) {
     u64 b = (n + threads - 1) / threads;
     if (b < 1) b = 1;
@@ -324,10 +399,10 @@ int bits_for(u64 I) {
 // K1 driver
 // ===========================================================================
 flycoo_status build_flycoo(Tensor &t, const u32 *d_idx, const float *d_vals,
-                           std::vector<std::vector<u32>> &row_ptr_host, cudaStream_t s) {
+                           std::vector<std::vector<u32>> &ss_ptr_host, cudaStream_t s) {
     const int N = t.N;
     const u64 nnz = t.nnz;
-    row_ptr_host.assign(N, {});
+    ss_ptr_host.assign(N, {});
     // 1. coordinate range check
     DevBuf err;
     FLY_TRY(err.alloc(sizeof(u32)));
@@ -355,7 +430,6 @@ flycoo_status build_flycoo(Tensor &t, const u32 *d_idx, const float *d_vals,
     FLY_TRY(b_vtmp.alloc(nnz * 4));
     FLY_TRY(b_counts.alloc(256 * ntiles * 4));
     u64 scan_words = scan_scratch_words(std::max<u64>(256 * ntiles, 1));
-    for (int w = 0; w < N; ++w) scan_words = std::max(scan_words, scan_scratch_words(t.dims[w] + 1));
     FLY_TRY(b_scan.alloc(scan_words * 4));
     std::vector<DevBuf> pi(N);
     for (int n = 0; n < N; ++n) FLY_TRY(pi[n].alloc(nnz * 4));
@@ -364,18 +438,21 @@ flycoo_status build_flycoo(Tensor &t, const u32 *d_idx, const float *d_vals,
     u32 *ktmp = b_ktmp.as<u32>(), *vtmp = b_vtmp.as<u32>();
     const unsigned grid = grid_for(nnz);
     if (nnz) iota_kernel<<<grid, 256, 0, s>>>(vals, nnz);
+    // super-shard ids: ss_w = c_w div m_w, k_w = ceil(I_w / m_w) of them
+    std::vector<u64> kss(N);
+    for (int w = 0; w < N; ++w) kss[w] = (t.dims[w] + t.mode[w].m - 1) / t.mode[w].m;
     std::vector<DevBuf> rp(N);
     auto sort_by_mode = [&](int w) -> flycoo_status {
-        if (nnz) gather_kernel<<<grid, 256, 0, s>>>(d_idx + (u64)w * nnz, vals, keys, nnz);
+        if (nnz) gather_div_kernel<<<grid, 256, 0, s>>>(d_idx + (u64)w * nnz, vals, keys, nnz, (u32)t.mode[w].m);
         FLY_TRY_CUDA(cudaGetLastError());
         return stable_sort_pairs(&keys, &vals, &ktmp, &vtmp, b_counts.as<u32>(), b_scan.as<u32>(), nnz,
-                                 bits_for(t.dims[w]), s);
+                                 bits_for(kss[w]), s);
     };
     auto finish_mode = [&](int n) -> flycoo_status {
-        // vals = pi_n, keys = c_n in L_n order
+        // vals = pi_n, keys = super-shard ids of mode n in L_n order
         FLY_TRY_CUDA(cudaMemcpyAsync(pi[n].p, vals, nnz * 4, cudaMemcpyDeviceToDevice, s));
-        FLY_TRY(rp[n].alloc((t.dims[n] + 1) * 4));
-        row_ptr_kernel<<<grid_for(nnz + 1), 256, 0, s>>>(keys, nnz, t.dims[n], rp[n].as<u32>());
+        FLY_TRY(rp[n].alloc((kss[n] + 1) * 4));
+        row_ptr_kernel<<<grid_for(nnz + 1), 256, 0, s>>>(keys, nnz, kss[n], rp[n].as<u32>());
         FLY_TRY_CUDA(cudaGetLastError());
         return FLYCOO_OK;
     };
@@ -387,12 +464,35 @@ flycoo_status build_flycoo(Tensor &t, const u32 *d_idx, const float *d_vals,
         FLY_TRY(finish_mode(n));
     }
 
-    // 3. remap permutations: next_n[p] = pos_{n+1}[pi_n[p]]
+    // 3. host: super-shard pointers -> shards, tiles, schedules (Section III-A, Algorithm 3)
+    for (int n = 0; n < N; ++n) {
+        ss_ptr_host[n].resize(kss[n] + 1);
+        FLY_TRY_CUDA(cudaMemcpyAsync(ss_ptr_host[n].data(), rp[n].p, (kss[n] + 1) * 4,
+                                     cudaMemcpyDeviceToHost, s));
+    }
+    FLY_TRY_CUDA(cudaStreamSynchronize(s));
+    for (int n = 0; n < N; ++n) FLY_TRY(partition_mode(t, n, ss_ptr_host[n], s));
+
+    // 4. inside each layout tile, order the positions by output index (stable)
+    for (int n = 0; n < N && nnz; ++n) {
+        const std::vector<u32> &tp = t.mode[n].tile_ptr;
+        DevBuf d_tp;
+        FLY_TRY(d_tp.alloc(tp.size() * 4));
+        FLY_TRY_CUDA(cudaMemcpyAsync(d_tp.p, tp.data(), tp.size() * 4, cudaMemcpyHostToDevice, s));
+        tile_sort_kernel<<<(unsigned)(tp.size() - 1), 256, 0, s>>>(pi[n].as<u32>(), vtmp, d_tp.as<u32>(),
+                                                                    d_idx + (u64)n * nnz, (u32)t.mode[n].m);
+        FLY_TRY_CUDA(cudaGetLastError());
+        FLY_TRY_CUDA(cudaMemcpyAsync(pi[n].p, vtmp, nnz * 4, cudaMemcpyDeviceToDevice, s));
+        FLY_TRY_CUDA(cudaStreamSynchronize(s)); // d_tp goes out of scope
+    }
+
+    // 5. remap permutations: next_n[p] = pos_{n+1}[pi_n[p]]
     {
         u32 *pos = ktmp; // scratch
         for (int n = 0; n < N; ++n) {
             const int m = (n + 1) % N;
-            FLY_TRY(t.mode[n].d_next.alloc(nnz * 4));
+            // +16 bytes: tile loads round the slot range out to 16-byte boundaries
+            FLY_TRY(t.mode[n].d_next.alloc(nnz * 4 + 16));
             if (nnz) {
                 inverse_kernel<<<grid, 256, 0, s>>>(pi[m].as<u32>(), pos, nnz);
                 gather_kernel<<<grid, 256, 0, s>>>(pos, pi[n].as<u32>(), t.mode[n].d_next.as<u32>(), nnz);
@@ -401,7 +501,7 @@ flycoo_status build_flycoo(Tensor &t, const u32 *d_idx, const float *d_vals,
         }
     }
 
-    // 4. element buffers, tensor stored in L_0
+    // 6. element buffers, tensor stored in L_0
     const u64 eb = (u64)t.elem_words * 4;
     FLY_TRY(t.elem[0].alloc(nnz * eb));
     FLY_TRY(t.elem[1].alloc(nnz * eb));
@@ -412,13 +512,6 @@ flycoo_status build_flycoo(Tensor &t, const u32 *d_idx, const float *d_vals,
     }
     t.cur = 0;
     t.layout = 0;
-
-    // 5. row pointers to the host for the partition bookkeeping
-    for (int n = 0; n < N; ++n) {
-        row_ptr_host[n].resize(t.dims[n] + 1);
-        FLY_TRY_CUDA(cudaMemcpyAsync(row_ptr_host[n].data(), rp[n].p, (t.dims[n] + 1) * 4,
-                                     cudaMemcpyDeviceToHost, s));
-    }
     FLY_TRY_CUDA(cudaStreamSynchronize(s));
     return FLYCOO_OK;
 }

@@ -1,7 +1,7 @@
 // static_scratch.cu -- flycoo_spmttkrp_static_scratch: the fused spMTTKRP +
-// remap pass with its scratch (the partial rows of the rows that straddle
-// shard boundaries) in a fixed, file-scope device array instead of the buffer
-// that flycoo_create allocates for the handle.
+// remap pass with its scratch (the per-shard row blocks of super-shards that
+// span several shards) in a fixed, file-scope device array instead of the
+// buffer that flycoo_create allocates for the handle.
 //
 // Host code must not pass g_static_scratch itself to a kernel: on the host that
 // name is only a stand-in object, not a device address.  The device address is
@@ -104,12 +104,14 @@ extern "C" flycoo_status flycoo_spmttkrp_static_scratch(flycoo_handle h, int mod
         return FLYCOO_ERR_LAYOUT;
     }
     const ModeMeta &md = t.mode[mode];
-    // head and tail partial rows: S x R floats each
-    const size_t need = 2 * (size_t)md.S * (size_t)R;
+    // one row block (m rows x R floats) per shard
+    const size_t need = (size_t)md.S * (size_t)md.m * (size_t)R;
     if (need > kStaticScratchFloats) {
-        set_error("flycoo_spmttkrp_static_scratch: mode %d has %llu shards; rank %d needs %zu bytes of scratch, "
-                  "the static scratch holds %zu bytes (use flycoo_spmttkrp or a larger shard size g)",
-                  mode, (unsigned long long)md.S, R, need * sizeof(float), kStaticScratchBytes);
+        set_error("flycoo_spmttkrp_static_scratch: mode %d has %llu shards of %llu-row super-shards; rank %d "
+                  "needs %zu bytes of scratch, the static scratch holds %zu bytes (use flycoo_spmttkrp or a "
+                  "larger shard size g)",
+                  mode, (unsigned long long)md.S, (unsigned long long)md.m, R, need * sizeof(float),
+                  kStaticScratchBytes);
         return FLYCOO_ERR_INVALID_ARG;
     }
     ScratchDeviceGuard dg(t.device);
@@ -128,23 +130,25 @@ extern "C" flycoo_status flycoo_spmttkrp_static_scratch(flycoo_handle h, int mod
     for (int q = 1; q < t.N; ++q) a.Y[q - 1] = h_factors[(mode + q) % t.N];
     a.out = d_out;
     a.shard_ptr = md.d_shard_ptr.as<u32>();
-    a.first_row = md.d_first_row.as<u32>();
-    a.last_row = md.d_last_row.as<u32>();
+    a.shard_ss = md.d_shard_ss.as<u32>();
+    a.ss_shard_ptr = md.d_ss_shard_ptr.as<u32>();
     a.bin_ptr = md.d_bin_ptr.as<u32>();
     a.bin_items = md.d_items.as<u32>();
-    a.p_head = scratch;
-    a.p_tail = scratch + (size_t)md.S * R;
+    a.partials = scratch;
+    a.err = t.err.as<u32>();
     a.I_out = (u32)t.dims[mode];
+    a.m = (u32)md.m;
     a.S = (u32)md.S;
     a.bins = t.bins;
     FLY_TRY(launch_fused(t.N, R, fdt, a, s));
     FixupArgs f{};
-    f.bnd = md.d_bnd.as<u32>();
-    f.nb = (u32)(md.bnd.size() / 3);
-    f.first_row = md.d_first_row.as<u32>();
-    f.p_head = a.p_head;
-    f.p_tail = a.p_tail;
+    f.items = md.d_k4.as<u32>();
+    f.nitems = (u32)md.k4_items.size();
+    f.ss_shard_ptr = md.d_ss_shard_ptr.as<u32>();
+    f.partials = a.partials;
     f.out = d_out;
+    f.I_out = a.I_out;
+    f.m = a.m;
     FLY_TRY(launch_fixup(R, f, s));
     if (next_mode >= 0) {
         t.cur = 1 - t.cur;

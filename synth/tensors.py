@@ -82,6 +82,18 @@ WORKLOADS: Dict[str, Workload] = {
         factor_law="normal_over_sqrt_r",
         stands_in_for="Nell-2 (FROSTT)",
     ),
+    # The same laws at 16M nonzeros: a profiling case that still exceeds L2
+    # (two 256 MB element buffers) but keeps an ncu capture to ~1 GB.
+    "nell2like_12000x9000x29000_16m_r32": Workload(
+        name="nell2like_12000x9000x29000_16m_r32",
+        dims=(12_000, 9_000, 29_000),
+        nnz=16_000_000,
+        index_laws=(("zipf", 1.1),) * 3,
+        value_law="lognormal",
+        rank=32,
+        factor_law="normal_over_sqrt_r",
+        stands_in_for="Nell-2 (FROSTT), reduced for profiling",
+    ),
     # Delicious-like 4-mode tensor for the BF16-vs-FP32 precision study.
     "delicious4d_1.2mx1.2mx50kx10k_140m_r32": Workload(
         name="delicious4d_1.2mx1.2mx50kx10k_140m_r32",

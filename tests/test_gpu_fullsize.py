@@ -64,11 +64,18 @@ def test_layout_properties_full_size(data):
             T.remap(n)
         li, lv = T.export_layout()
         c = to_np(li).view(np.uint32)
-        # sorted by the cyclic key (c_n, c_{n-1}, c_{n+1}): compare adjacent positions
-        k0, k1, k2 = c[n].astype(np.int64), c[(n - 1) % N].astype(np.int64), c[(n + 1) % N].astype(np.int64)
-        d0, d1, d2 = np.diff(k0), np.diff(k1), np.diff(k2)
-        ok = (d0 > 0) | ((d0 == 0) & ((d1 > 0) | ((d1 == 0) & (d2 > 0))))
-        assert ok.all(), "layout not strictly ordered by the cyclic key (coordinates are distinct)"
+        info = T.info
+        m, tile = info["m"], info["tile"]
+        # super-shards of mode n are contiguous and ascending (ss_n = c_n div m_n)
+        assert np.all(np.diff(c[n].astype(np.int64) // m[n]) >= 0)
+        # every layout tile (tile positions from each shard start) is sorted by c_n
+        _, sp, _ = T.export_partition(n)
+        starts = np.concatenate([np.arange(a, b, tile) for a, b in zip(sp[:-1], sp[1:])]).astype(np.int64)
+        tile_id = np.zeros(c.shape[1], dtype=np.int64)
+        tile_id[starts[1:]] = 1
+        tile_id = np.cumsum(tile_id)
+        d = np.diff(c[n].astype(np.int64))
+        assert np.all(d[tile_id[1:] == tile_id[:-1]] >= 0), "a layout tile is not sorted by c_n"
         if n == 0:
             # a permutation of the input: same coordinates and values as a multiset
             key_in = (idx[0].astype(np.int64) * WL.dims[1] + idx[1]) * WL.dims[2] + idx[2]
@@ -81,6 +88,6 @@ def test_layout_properties_full_size(data):
     info = T.info
     # Section III-A shard count: S_n = sum_j ceil(|SS_n,j| / g)
     for n in range(N):
-        ss, sp, fr, lr = T.export_partition(n)
+        ss, sp, sss = T.export_partition(n)
         sizes = np.diff(ss.astype(np.int64))
         assert info["shards"][n] == int(np.sum((sizes + info["g"] - 1) // info["g"]))

@@ -42,6 +42,7 @@ LAYOUT_CASES = [
     ((4, 3, 3, 2, 2), 100, 2, "uniform", False, (2, 1, 1, 1, 1), 5, 4),
     ((50, 2, 3), 150, 3, "zipf", True, (7, 1, 1), 1, 2),
     ((1000, 800, 600), 20000, 4, "zipf", True, (0, 0, 0), 0, 0),
+    ((300, 200, 250), 30000, 6, "zipf", True, (128, 5, 1), 777, 13),
     ((3, 1, 700), 700, 5, "uniform", True, (1, 1, 10), 64, 9),
 ]
 
@@ -56,11 +57,10 @@ def test_layout_partition_schedule_bitexact(P, case):
     assert info["nnz"] == nnz and info["layout_mode"] == 0
     ref = oracle.flycoo_layout(idx, dims, info["m"], info["g"], info["bins"])
     for n in range(N):
-        ss, sp, fr, lr = T.export_partition(n)
+        ss, sp, sss = T.export_partition(n)
         np.testing.assert_array_equal(ss, ref[n]["ss_ptr"])
         np.testing.assert_array_equal(sp, ref[n]["shard_ptr"])
-        np.testing.assert_array_equal(fr, ref[n]["first_row"])
-        np.testing.assert_array_equal(lr, ref[n]["last_row"])
+        np.testing.assert_array_equal(sss, ref[n]["shard_ss"])
         for which, key in ((0, "ss_bins"), (1, "shard_bins")):
             bp, items = T.export_schedule(n, which)
             np.testing.assert_array_equal(bp, ref[n][key][0])
@@ -81,6 +81,7 @@ def test_layout_partition_schedule_bitexact(P, case):
 MTTKRP_CASES = [
     # dims, nnz, law, R, g, bins
     ((1000, 800, 600), 100_000, "uniform", 16, 0, 0),
+    ((5000, 3000, 2000), 80_000, "zipf", 32, 2048, 50),
     ((200, 150, 120), 30_000, "zipf", 32, 512, 37),
     ((300, 50, 400), 25_000, "zipf", 64, 1000, 64),
     ((60, 70, 50, 40), 20_000, "zipf", 32, 700, 20),

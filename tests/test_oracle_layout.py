@@ -28,22 +28,38 @@ def test_layout_is_sorted_permutation(dims, nnz, seed):
 
 
 @pytest.mark.parametrize("dims,nnz,seed", CASES)
-def test_next_layout_is_stable_counting_sort(dims, nnz, seed):
-    # Under the cyclic key, L_{n+1} is L_n stably sorted by c_{n+1} alone: the
-    # remap of Algorithm 2 is a stable bucket scatter by the next output index.
+@pytest.mark.parametrize("widths", ["ones", "mixed"])
+def test_next_layout_is_stable_counting_sort(dims, nnz, seed, widths):
+    # Under the cyclic key, L_{n+1} is L_n stably sorted by the super-shard id
+    # of mode n+1 alone: the remap of Algorithm 2 is a stable bucket scatter
+    # into the next mode's super-shards.
     idx, _ = random_coo(dims, nnz, seed=seed, distinct=False)
     N = len(dims)
-    orders = [oracle.layout_order(idx, n) for n in range(N)]
+    m = [1] * N if widths == "ones" else [max(1, d // 3) for d in dims]
+    ss = [idx[w] // m[w] for w in range(N)]
+    orders = [oracle.layout_order(idx, n, m) for n in range(N)]
     for n in range(N):
-        m = (n + 1) % N
+        nx = (n + 1) % N
         prev = orders[n]
-        stable = prev[np.argsort(idx[m][prev], kind="stable")]
-        assert np.array_equal(stable, orders[m])
+        stable = prev[np.argsort(ss[nx][prev], kind="stable")]
+        assert np.array_equal(stable, orders[nx])
+        # super-shards of mode n are contiguous and ascending in L_n
+        assert np.all(np.diff(ss[n][orders[n]].astype(np.int64)) >= 0)
     # and L_0 is the input order stably sorted by modes 1, 2, ..., N-1, 0 in turn
     cur = np.arange(nnz, dtype=np.uint32)
     for w in list(range(1, N)) + [0]:
-        cur = cur[np.argsort(idx[w][cur], kind="stable")]
+        cur = cur[np.argsort(ss[w][cur], kind="stable")]
     assert np.array_equal(cur, orders[0])
+
+
+def test_layout_order_with_unit_widths_sorts_by_coordinates():
+    # with m_w = 1 every super-shard id is the coordinate: L_n is ordered by
+    # (c_n, c_{n-1}, ..., c_{n+1}) and rows are contiguous
+    idx, _ = random_coo((9, 8, 7), 300, seed=4, distinct=True)
+    for n in range(3):
+        o = oracle.layout_order(idx, n, [1, 1, 1])
+        keys = list(zip(idx[n][o], idx[(n - 1) % 3][o], idx[(n + 1) % 3][o]))
+        assert keys == sorted(keys)
 
 
 @pytest.mark.parametrize("dims,nnz,seed", CASES)
@@ -144,16 +160,41 @@ def test_lpt_within_four_thirds_of_optimum():
         assert load.max() <= (4.0 / 3.0 - 1.0 / (3 * nb)) * opt + 1e-9
 
 
-def test_flycoo_layout_shard_rows():
+def test_flycoo_layout_shards_lie_in_their_super_shard():
     dims = (40, 9, 8)
+    m = [5, 2, 3]
     idx, _ = random_coo(dims, 300, seed=21, law="zipf")
-    modes = oracle.flycoo_layout(idx, dims, [5, 2, 3], 16, 6)
+    modes = oracle.flycoo_layout(idx, dims, m, 16, 6)
     for n, md in enumerate(modes):
-        rows = idx[n][md["order"]]
+        ss = idx[n][md["order"]] // m[n]
         sp = md["shard_ptr"].astype(np.int64)
-        assert np.array_equal(md["first_row"], rows[sp[:-1]])
-        assert np.array_equal(md["last_row"], rows[sp[1:] - 1])
+        for q in range(sp.size - 1):
+            assert np.all(ss[sp[q]:sp[q + 1]] == md["shard_ss"][q])
+            assert sp[q + 1] - sp[q] <= 16
         ptr, items = md["shard_bins"]
         assert np.array_equal(np.sort(items), np.arange(sp.size - 1))
         ptr, items = md["ss_bins"]
         assert np.array_equal(np.sort(items), np.arange(md["ss_ptr"].size - 1))
+
+
+@pytest.mark.parametrize("tile", [1, 4, 7, 512])
+def test_stored_order_sorts_tiles_and_keeps_shards(tile):
+    # the stored order only permutes positions inside each layout tile, and each
+    # tile comes out sorted by output coordinate with ties in key order
+    dims = (40, 12, 9)
+    m = [8, 3, 4]
+    idx, _ = random_coo(dims, 500, seed=31, law="zipf", distinct=False)
+    modes = oracle.flycoo_layout(idx, dims, m, 37, 5, tile=tile)
+    for n, md in enumerate(modes):
+        key_order = oracle.layout_order(idx, n, m)
+        sp = md["shard_ptr"].astype(np.int64)
+        pos_in_key = oracle.inverse(key_order)
+        for q in range(sp.size - 1):
+            for a in range(sp[q], sp[q + 1], tile):
+                b = min(a + tile, sp[q + 1])
+                seg = md["order"][a:b]
+                assert sorted(seg.tolist()) == sorted(key_order[a:b].tolist())
+                r = idx[n][seg]
+                assert np.all(np.diff(r.astype(np.int64)) >= 0)
+                same = np.diff(r.astype(np.int64)) == 0
+                assert np.all(np.diff(pos_in_key[seg].astype(np.int64))[same] > 0)
