@@ -306,10 +306,13 @@ __global__ void __launch_bounds__(256, kBlocksPerSM) fused_mttkrp_remap_kernel(c
         u32 crow = kInvalidRow;
         bool first = true;
         if (!timed_out) {
-            for (u32 j0 = 0; j0 < chunk; j0 += C::SUB) {
+            // ping-pong batches: the gathers of batch b+1 are in flight while batch b is consumed
+            struct Batch {
                 uint4 raw[C::SUB][N - 1];
                 u32 row[C::SUB];
                 float val[C::SUB];
+            };
+            auto load_batch = [&](u32 j0, Batch &B) {
 #pragma unroll
                 for (int u = 0; u < C::SUB; ++u) {
                     const u32 p = lo + j0 + u;
@@ -325,24 +328,26 @@ __global__ void __launch_bounds__(256, kBlocksPerSM) fused_mttkrp_remap_kernel(c
                         w[4 * c + 2] = x.z;
                         w[4 * c + 3] = x.w;
                     }
-                    row[u] = v ? min(w[0] - row_base, (u32)M - 1u) : kInvalidRow;
-                    val[u] = __uint_as_float(w[N]);
+                    B.row[u] = v ? min(w[0] - row_base, (u32)M - 1u) : kInvalidRow;
+                    B.val[u] = __uint_as_float(w[N]);
 #pragma unroll
-                    for (int t = 1; t < N; ++t) raw[u][t - 1] = __ldg(Yp[t - 1] + (size_t)w[t] * RV);
+                    for (int t = 1; t < N; ++t) B.raw[u][t - 1] = __ldg(Yp[t - 1] + (size_t)w[t] * RV);
                 }
+            };
+            auto run_batch = [&](const Batch &B) {
 #pragma unroll
                 for (int u = 0; u < C::SUB; ++u) {
-                    if (row[u] == kInvalidRow) continue;
+                    if (B.row[u] == kInvalidRow) continue;
                     float prod[VEC];
-                    widen<BF16>(raw[u][0], prod);
+                    widen<BF16>(B.raw[u][0], prod);
 #pragma unroll
                     for (int t = 1; t < N - 1; ++t) {
                         float f[VEC];
-                        widen<BF16>(raw[u][t], f);
+                        widen<BF16>(B.raw[u][t], f);
 #pragma unroll
                         for (int v = 0; v < VEC; ++v) prod[v] *= f[v];
                     }
-                    if (row[u] != crow) {
+                    if (B.row[u] != crow) {
                         if (crow != kInvalidRow) {
                             if (first) {
                                 store_vec<VEC>(my_hacc, racc);
@@ -355,13 +360,23 @@ __global__ void __launch_bounds__(256, kBlocksPerSM) fused_mttkrp_remap_kernel(c
                                 store_vec<VEC>(dst, racc);
                             }
                         }
-                        crow = row[u];
+                        crow = B.row[u];
 #pragma unroll
                         for (int v = 0; v < VEC; ++v) racc[v] = 0.f;
                     }
 #pragma unroll
-                    for (int v = 0; v < VEC; ++v) racc[v] = fmaf(val[u], prod[v], racc[v]);
+                    for (int v = 0; v < VEC; ++v) racc[v] = fmaf(B.val[u], prod[v], racc[v]);
                 }
+            };
+            Batch A, Bb;
+            load_batch(0u, A);
+            for (u32 j0 = 0; j0 < chunk; j0 += 2 * C::SUB) {
+                const bool more1 = j0 + C::SUB < chunk;
+                if (more1) load_batch(j0 + C::SUB, Bb);
+                run_batch(A);
+                if (!more1) break;
+                if (j0 + 2 * C::SUB < chunk) load_batch(j0 + 2 * C::SUB, A);
+                run_batch(Bb);
             }
         }
         // slice summary: a single run in the head slot, else the last run in the tail slot
