@@ -14,8 +14,9 @@
  *  - Dense matrices are row-major.  Factor matrix Y_w is I_w x R; an output
  *    M_n is I_n x R in FP32.  Coordinates are 0-based (Section II-A).
  *  - Work is ordered on the given stream (a cudaStream_t; NULL is the legacy
- *    default stream).  Only flycoo_create, flycoo_sync, the export_* calls
- *    that fill host buffers and flycoo_timing_read wait for the stream.
+ *    default stream).  Only flycoo_create, flycoo_sync, flycoo_cpopt_grad
+ *    (for its loss), the export_* calls that fill host buffers and
+ *    flycoo_timing_read wait for the stream.
  *  - Every entry point returns a flycoo_status and never aborts or traps;
  *    flycoo_last_error() then describes the failure (per calling thread).
  *  - A handle is not thread-safe: calls on one handle must not overlap.
@@ -162,6 +163,41 @@ flycoo_status flycoo_spmttkrp(flycoo_handle h, int mode, const void *const *h_fa
 flycoo_status flycoo_spmttkrp_static_scratch(flycoo_handle h, int mode, const void *const *h_factors,
                                              flycoo_dtype fdt, int R, float *d_out, int next_mode,
                                              flycoo_stream_t stream);
+
+/* ------------------------------------------------------------------------ */
+/* flycoo_mttkrp_adjoint -- adjoint of flycoo_spmttkrp with respect to the   */
+/* factors (the elementwise equation of Section IV is linear in each input   */
+/* factor).  For an upstream gradient G = d loss / d M_mode (I_mode x R):    */
+/*   dY_w = spMTTKRP_w(X, Y with Y_mode replaced by G)      for each w != mode */
+/* Each dY_w is one fused pass of mode w in layout L_w, so it reuses that    */
+/* mode's shards without atomics (and remaps as it goes).  The tensor is     */
+/* first remapped to L_{mode+1} if it is elsewhere and ends in L_mode.       */
+/*  h_factors   HOST array of N DEVICE FP32 factor pointers (entry mode unused) */
+/*  d_gout      I_mode x R FP32 upstream gradient                            */
+/*  h_gfactors  HOST array of N DEVICE pointers, I_w x R FP32 outputs,       */
+/*              overwritten; NULL entries (and entry mode) are skipped       */
+/* Errors: INVALID_ARG, UNSUPPORTED (rank), CUDA.                            */
+/* ------------------------------------------------------------------------ */
+flycoo_status flycoo_mttkrp_adjoint(flycoo_handle h, int mode, const float *const *h_factors, int R,
+                                    const float *d_gout, float *const *h_gfactors,
+                                    flycoo_stream_t stream);
+
+/* ------------------------------------------------------------------------ */
+/* flycoo_cpopt_grad -- weighted CP on the observed entries (CP-OPT loss):   */
+/*   L = 1/2 sum_x (x - m_x)^2,   m_x = sum_r prod_w Y_w[c_w(x), r] (Eq. 1)  */
+/*   dL/dY_n = -spMTTKRP_n with each value x replaced by its residual x - m_x */
+/* One fused pass per mode (N passes, each remapping to the next layout, so  */
+/* the tensor ends where it started); the residual is formed inside the      */
+/* pass from the gathered rows.  FP32 arithmetic, the loss summed in FP64 in */
+/* a fixed order.                                                            */
+/*  h_factors  HOST array of N DEVICE FP32 factor pointers (I_w x R)         */
+/*  h_grads    HOST array of N DEVICE FP32 outputs (I_w x R), overwritten    */
+/*  h_loss     HOST double; NULL skips the loss (and the wait for it)        */
+/* Waits for `stream` when h_loss is given.  Errors: INVALID_ARG,            */
+/* UNSUPPORTED (rank), CUDA.                                                 */
+/* ------------------------------------------------------------------------ */
+flycoo_status flycoo_cpopt_grad(flycoo_handle h, const float *const *h_factors, int R,
+                                float *const *h_grads, double *h_loss, flycoo_stream_t stream);
 
 /* ------------------------------------------------------------------------ */
 /* flycoo_remap -- dynamic tensor remapping alone (Section III-B): move the  */

@@ -8,6 +8,7 @@ from ._native import (  # noqa: F401
     BF16,
     F32,
     FlycooError,
+    flycoo_cpopt_grad,
     flycoo_create,
     flycoo_destroy,
     flycoo_export_layout,
@@ -16,6 +17,7 @@ from ._native import (  # noqa: F401
     flycoo_export_schedule,
     flycoo_get_info,
     flycoo_last_error,
+    flycoo_mttkrp_adjoint,
     flycoo_remap,
     flycoo_spmttkrp,
     flycoo_spmttkrp_static_scratch,
@@ -25,3 +27,4 @@ from ._native import (  # noqa: F401
     make_params,
 )
 from .flycoo import FlycooTensor  # noqa: F401
+from .autograd import CPOPTLoss, SpMTTKRP, cpopt_loss, spmttkrp  # noqa: F401

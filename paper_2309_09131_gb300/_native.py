@@ -65,6 +65,8 @@ def lib():
             "flycoo_spmttkrp_static_scratch": [P, I, P, I, I, P, I, P],
             "flycoo_remap": [P, I, P],
             "flycoo_sync": [P, P],
+            "flycoo_mttkrp_adjoint": [P, I, P, I, P, P, P],
+            "flycoo_cpopt_grad": [P, P, I, P, P, P],
             "flycoo_get_info": [P, P],
             "flycoo_export_layout": [P, P, P, P],
             "flycoo_export_partition": [P, I, P, P, P],
@@ -198,6 +200,39 @@ def _spmttkrp_args(mode, factors, out):
     if out.dim() != 2 or out.shape[1] != R:
         raise ValueError("out must be [I_mode, R]")
     return ptrs, fdt, R, po
+
+
+def _ptr_array(tensors, dtypes, what, skip=-1, allow_none=False):
+    arr = (ctypes.c_void_p * len(tensors))()
+    for w, t in enumerate(tensors):
+        if w == skip or (allow_none and t is None):
+            continue
+        arr[w] = _dev_ptr(t, dtypes, f"{what} {w}")
+    return arr
+
+
+def flycoo_mttkrp_adjoint(h, mode: int, factors: Sequence[torch.Tensor], gout: torch.Tensor,
+                          gfactors: Sequence[Optional[torch.Tensor]], stream=None) -> None:
+    """dY_w = spMTTKRP_w(X, Y with Y_mode := gout) into ``gfactors[w]`` (FP32;
+    None entries skipped)."""
+    R = gout.shape[1]
+    F = _ptr_array(factors, (torch.float32,), "factor", skip=mode)
+    Gp = _dev_ptr(gout, (torch.float32,), "gout")
+    GF = _ptr_array(gfactors, (torch.float32,), "gradient", skip=mode, allow_none=True)
+    _check(lib().flycoo_mttkrp_adjoint(h, int(mode), F, int(R), Gp, GF, _stream(stream)))
+
+
+def flycoo_cpopt_grad(h, factors: Sequence[torch.Tensor], grads: Sequence[torch.Tensor], stream=None,
+                      want_loss: bool = True):
+    """CP-OPT loss 1/2 sum (x - m_x)^2 over the nonzeros and its gradients
+    (written to ``grads``); returns the loss (float) or None."""
+    R = factors[0].shape[1]
+    F = _ptr_array(factors, (torch.float32,), "factor")
+    Gr = _ptr_array(grads, (torch.float32,), "gradient")
+    loss = ctypes.c_double()
+    _check(lib().flycoo_cpopt_grad(h, F, int(R), Gr, ctypes.byref(loss) if want_loss else None,
+                                   _stream(stream)))
+    return loss.value if want_loss else None
 
 
 def flycoo_remap(h, next_mode: int, stream=None) -> None:

@@ -232,6 +232,7 @@ extern "C" flycoo_status flycoo_create(int N, const uint64_t *h_dims, uint64_t n
     FLY_TRY(build_flycoo(*t, d_idx, d_vals, ss_ptr, s));
     for (int n = 0; n < N; ++n) t->max_S = std::max<u64>(t->max_S, t->mode[n].S);
     FLY_TRY(t->partials.alloc(std::max<u64>(t->max_S, 1) * t->max_rows * kMaxRank * sizeof(float)));
+    FLY_TRY(t->loss_part.alloc((size_t)t->bins * sizeof(double)));
     FLY_TRY(t->err.alloc(sizeof(u32)));
     FLY_TRY_CUDA(cudaMemsetAsync(t->err.p, 0, sizeof(u32), s));
     FLY_TRY_CUDA(cudaStreamSynchronize(s));
@@ -368,6 +369,152 @@ extern "C" flycoo_status flycoo_sync(flycoo_handle h, flycoo_stream_t stream) {
         FLY_TRY_CUDA(cudaStreamSynchronize(s));
         set_error("flycoo_sync: a bounded device wait gave up (error word 0x%x)", e);
         return FLYCOO_ERR_TIMEOUT;
+    }
+    return FLYCOO_OK;
+}
+
+// One fused pass of mode `mode` in its layout: spMTTKRP (Yout == nullptr) or the
+// CP-OPT gradient pass; fused remap to the next layout; then K4.
+static flycoo_status run_pass(Tensor &t, int mode, const void *const *F, flycoo_dtype fdt, int R, float *d_out,
+                              const void *Yout, double *loss_part, cudaStream_t s) {
+    const ModeMeta &md = t.mode[mode];
+    if (t.nnz == 0) {
+        FLY_TRY_CUDA(cudaMemsetAsync(d_out, 0, (size_t)t.dims[mode] * R * sizeof(float), s));
+        t.layout = (mode + 1) % t.N;
+        return FLYCOO_OK;
+    }
+    FusedArgs a{};
+    a.elem_in = t.elem[t.cur].p;
+    a.elem_out = t.elem[1 - t.cur].p;
+    a.next = md.d_next.as<u32>();
+    for (int q = 1; q < t.N; ++q) a.Y[q - 1] = F[(mode + q) % t.N];
+    a.out = d_out;
+    a.shard_ptr = md.d_shard_ptr.as<u32>();
+    a.shard_ss = md.d_shard_ss.as<u32>();
+    a.ss_shard_ptr = md.d_ss_shard_ptr.as<u32>();
+    a.bin_ptr = md.d_bin_ptr.as<u32>();
+    a.bin_items = md.d_items.as<u32>();
+    a.partials = t.partials.as<float>();
+    a.err = t.err.as<u32>();
+    a.Yout = Yout;
+    a.loss_part = loss_part;
+    a.I_out = (u32)t.dims[mode];
+    a.m = (u32)md.m;
+    a.S = (u32)md.S;
+    a.bins = t.bins;
+    FLY_TRY(launch_fused(t.N, R, fdt, a, s));
+    FixupArgs f{};
+    f.items = md.d_k4.as<u32>();
+    f.nitems = (u32)md.k4_items.size();
+    f.ss_shard_ptr = md.d_ss_shard_ptr.as<u32>();
+    f.partials = a.partials;
+    f.out = d_out;
+    f.I_out = a.I_out;
+    f.m = a.m;
+    FLY_TRY(launch_fixup(R, f, s));
+    t.cur = 1 - t.cur;
+    t.layout = (mode + 1) % t.N;
+    return FLYCOO_OK;
+}
+
+static flycoo_status check_fp32_factors(const Tensor &t, const void *const *F, int skip, int R, const char *who) {
+    if (R != 16 && R != 32 && R != 64) {
+        set_error("%s: rank %d not built (16, 32 or 64)", who, R);
+        return R > 0 ? FLYCOO_ERR_UNSUPPORTED : FLYCOO_ERR_INVALID_ARG;
+    }
+    if (!F) {
+        set_error("%s: factor array is NULL", who);
+        return FLYCOO_ERR_INVALID_ARG;
+    }
+    for (int w = 0; w < t.N; ++w) {
+        if (w == skip) continue;
+        if (!F[w] || (reinterpret_cast<uintptr_t>(F[w]) & 15u)) {
+            set_error("%s: factor %d is NULL or not 16-byte aligned", who, w);
+            return FLYCOO_ERR_INVALID_ARG;
+        }
+    }
+    return FLYCOO_OK;
+}
+
+extern "C" flycoo_status flycoo_mttkrp_adjoint(flycoo_handle h, int mode, const float *const *h_factors, int R,
+                                               const float *d_gout, float *const *h_gfactors,
+                                               flycoo_stream_t stream) {
+    clear_error();
+    if (!h || mode < 0 || mode >= h->N) {
+        set_error("flycoo_mttkrp_adjoint: bad handle or mode");
+        return FLYCOO_ERR_INVALID_ARG;
+    }
+    Tensor &t = *h;
+    FLY_TRY(check_fp32_factors(t, reinterpret_cast<const void *const *>(h_factors), mode, R, "flycoo_mttkrp_adjoint"));
+    if (!d_gout || (reinterpret_cast<uintptr_t>(d_gout) & 15u) || !h_gfactors) {
+        set_error("flycoo_mttkrp_adjoint: d_gout / h_gfactors NULL or d_gout not 16-byte aligned");
+        return FLYCOO_ERR_INVALID_ARG;
+    }
+    for (int w = 0; w < t.N; ++w)
+        if (w != mode && h_gfactors[w] && (reinterpret_cast<uintptr_t>(h_gfactors[w]) & 15u)) {
+            set_error("flycoo_mttkrp_adjoint: gradient %d not 16-byte aligned", w);
+            return FLYCOO_ERR_INVALID_ARG;
+        }
+    DeviceGuard dg(t.device);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    // the factor list of every pass: Y_w, with the output mode's slot holding G
+    std::vector<const void *> F(t.N);
+    for (int w = 0; w < t.N; ++w) F[w] = (w == mode) ? (const void *)d_gout : (const void *)h_factors[w];
+    const int first = (mode + 1) % t.N;
+    while (t.layout != first) {
+        FLY_TRY(launch_remap_step(t, t.layout, t.elem[t.cur].p, t.elem[1 - t.cur].p, s));
+        t.cur = 1 - t.cur;
+        t.layout = (t.layout + 1) % t.N;
+    }
+    for (int q = 1; q < t.N; ++q) {
+        const int w = (mode + q) % t.N;
+        if (h_gfactors[w]) {
+            FLY_TRY(run_pass(t, w, F.data(), FLYCOO_F32, R, h_gfactors[w], nullptr, nullptr, s));
+        } else {
+            FLY_TRY(launch_remap_step(t, w, t.elem[t.cur].p, t.elem[1 - t.cur].p, s));
+            t.cur = 1 - t.cur;
+            t.layout = (w + 1) % t.N;
+        }
+    }
+    return FLYCOO_OK;
+}
+
+extern "C" flycoo_status flycoo_cpopt_grad(flycoo_handle h, const float *const *h_factors, int R,
+                                           float *const *h_grads, double *h_loss, flycoo_stream_t stream) {
+    clear_error();
+    if (!h) {
+        set_error("flycoo_cpopt_grad: handle is NULL");
+        return FLYCOO_ERR_INVALID_ARG;
+    }
+    Tensor &t = *h;
+    FLY_TRY(check_fp32_factors(t, reinterpret_cast<const void *const *>(h_factors), -1, R, "flycoo_cpopt_grad"));
+    if (!h_grads) {
+        set_error("flycoo_cpopt_grad: h_grads is NULL");
+        return FLYCOO_ERR_INVALID_ARG;
+    }
+    for (int w = 0; w < t.N; ++w)
+        if (!h_grads[w] || (reinterpret_cast<uintptr_t>(h_grads[w]) & 15u)) {
+            set_error("flycoo_cpopt_grad: gradient %d is NULL or not 16-byte aligned", w);
+            return FLYCOO_ERR_INVALID_ARG;
+        }
+    DeviceGuard dg(t.device);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const void *const *F = reinterpret_cast<const void *const *>(h_factors);
+    double *lp = t.loss_part.as<double>();
+    if (t.nnz) FLY_TRY_CUDA(cudaMemsetAsync(lp, 0, (size_t)t.bins * sizeof(double), s));
+    const int start = t.layout;
+    for (int q = 0; q < t.N; ++q) {
+        const int n = (start + q) % t.N;
+        FLY_TRY(run_pass(t, n, F, FLYCOO_F32, R, h_grads[n], F[n], q == 0 ? lp : nullptr, s));
+    }
+    if (h_loss) {
+        std::vector<double> part(t.bins, 0.0);
+        if (t.nnz)
+            FLY_TRY_CUDA(cudaMemcpyAsync(part.data(), lp, (size_t)t.bins * sizeof(double), cudaMemcpyDeviceToHost, s));
+        FLY_TRY_CUDA(cudaStreamSynchronize(s));
+        double L = 0.0;
+        for (double x : part) L += x; // fixed order
+        *h_loss = L;
     }
     return FLYCOO_OK;
 }

@@ -193,9 +193,10 @@ struct TileCursor {
     }
 };
 
-template <int N, int R, bool BF16>
+template <int N, int R, bool BF16, bool CPOPT>
 __global__ void __launch_bounds__(256, kBlocksPerSM) fused_mttkrp_remap_kernel(const FusedArgs a) {
     using C = FusedCfg<N, R, BF16>;
+    static_assert(!(CPOPT && BF16), "the CP-OPT gradient pass takes FP32 factors");
     constexpr int VEC = C::VEC;
     constexpr int RV = R / VEC; // 16-byte chunks per factor row
     constexpr int CAP = C::CAP;
@@ -221,6 +222,9 @@ __global__ void __launch_bounds__(256, kBlocksPerSM) fused_mttkrp_remap_kernel(c
     const uint4 *Yp[N - 1];
 #pragma unroll
     for (int t = 0; t < N - 1; ++t) Yp[t] = static_cast<const uint4 *>(a.Y[t]) + k;
+    // CP-OPT: the output mode's own factor, for the model value at each nonzero
+    const uint4 *Yo = CPOPT ? static_cast<const uint4 *>(a.Yout) + k : nullptr;
+    double loss = 0.0;
     float *my_hacc = hacc + grp * R + k * VEC;
     float *my_tacc = tacc + grp * R + k * VEC;
 
@@ -308,7 +312,7 @@ __global__ void __launch_bounds__(256, kBlocksPerSM) fused_mttkrp_remap_kernel(c
         if (!timed_out) {
             // ping-pong batches: the gathers of batch b+1 are in flight while batch b is consumed
             struct Batch {
-                uint4 raw[C::SUB][N - 1];
+                uint4 raw[C::SUB][CPOPT ? N : N - 1];
                 u32 row[C::SUB];
                 float val[C::SUB];
             };
@@ -332,12 +336,12 @@ __global__ void __launch_bounds__(256, kBlocksPerSM) fused_mttkrp_remap_kernel(c
                     B.val[u] = __uint_as_float(w[N]);
 #pragma unroll
                     for (int t = 1; t < N; ++t) B.raw[u][t - 1] = __ldg(Yp[t - 1] + (size_t)w[t] * RV);
+                    if constexpr (CPOPT) B.raw[u][N - 1] = __ldg(Yo + (size_t)w[0] * RV);
                 }
             };
             auto run_batch = [&](const Batch &B) {
 #pragma unroll
                 for (int u = 0; u < C::SUB; ++u) {
-                    if (B.row[u] == kInvalidRow) continue;
                     float prod[VEC];
                     widen<BF16>(B.raw[u][0], prod);
 #pragma unroll
@@ -347,6 +351,22 @@ __global__ void __launch_bounds__(256, kBlocksPerSM) fused_mttkrp_remap_kernel(c
 #pragma unroll
                         for (int v = 0; v < VEC; ++v) prod[v] *= f[v];
                     }
+                    float coef = B.val[u];
+                    if constexpr (CPOPT) {
+                        // model value m = <Y_n[c_n], prod>: lane partials summed over the group
+                        // (every lane runs the shuffles, so out-of-slice slots take part too)
+                        float yo[VEC];
+                        widen<false>(B.raw[u][N - 1], yo);
+                        float mpart = 0.f;
+#pragma unroll
+                        for (int v = 0; v < VEC; ++v) mpart = fmaf(yo[v], prod[v], mpart);
+#pragma unroll
+                        for (int off = C::L / 2; off >= 1; off >>= 1) mpart += __shfl_xor_sync(0xffffffffu, mpart, off);
+                        const float e = B.val[u] - mpart;  // residual x - m
+                        if (B.row[u] != kInvalidRow && k == 0) loss += (double)e * (double)e;
+                        coef = -e;                          // dL/dY_n += -e * prod
+                    }
+                    if (B.row[u] == kInvalidRow) continue;
                     if (B.row[u] != crow) {
                         if (crow != kInvalidRow) {
                             if (first) {
@@ -365,7 +385,7 @@ __global__ void __launch_bounds__(256, kBlocksPerSM) fused_mttkrp_remap_kernel(c
                         for (int v = 0; v < VEC; ++v) racc[v] = 0.f;
                     }
 #pragma unroll
-                    for (int v = 0; v < VEC; ++v) racc[v] = fmaf(B.val[u], prod[v], racc[v]);
+                    for (int v = 0; v < VEC; ++v) racc[v] = fmaf(coef, prod[v], racc[v]);
                 }
             };
             Batch A, Bb;
@@ -449,6 +469,21 @@ __global__ void __launch_bounds__(256, kBlocksPerSM) fused_mttkrp_remap_kernel(c
         }
         cur.advance(a);
     }
+    if constexpr (CPOPT) {
+        // half the sum of squared residuals of this block, reduced in a fixed order
+        if (a.loss_part) {
+            __shared__ double wsum[C::WARPS];
+#pragma unroll
+            for (int off = 16; off >= 1; off >>= 1) loss += __shfl_xor_sync(0xffffffffu, loss, off);
+            if (lane == 0) wsum[warp] = loss;
+            __syncthreads();
+            if (tid == 0) {
+                double t = 0.0;
+                for (int w = 0; w < C::WARPS; ++w) t += wsum[w];
+                a.loss_part[blockIdx.x] = 0.5 * t;
+            }
+        }
+    }
 }
 
 // K4: rows of the super-shards that do not have exactly one shard: the sum of
@@ -477,10 +512,10 @@ static __global__ void __launch_bounds__(256) super_shard_fixup_kernel(const Fix
     }
 }
 
-template <int N, int R, bool BF16>
+template <int N, int R, bool BF16, bool CPOPT = false>
 flycoo_status launch_fused_t(const FusedArgs &a, cudaStream_t s) {
     using C = FusedCfg<N, R, BF16>;
-    auto kern = fused_mttkrp_remap_kernel<N, R, BF16>;
+    auto kern = fused_mttkrp_remap_kernel<N, R, BF16, CPOPT>;
     if (C::SMEM > 48 * 1024)
         FLY_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM));
     kern<<<a.bins, C::THREADS, C::SMEM, s>>>(a);
@@ -491,6 +526,20 @@ flycoo_status launch_fused_t(const FusedArgs &a, cudaStream_t s) {
 template <int N>
 flycoo_status launch_fused_dispatch(int R, flycoo_dtype dt, const FusedArgs &a, cudaStream_t s) {
     const bool bf = dt == FLYCOO_BF16;
+    if (a.Yout) { // CP-OPT gradient pass (FP32 factors)
+        if (bf) {
+            set_error("the CP-OPT gradient pass takes FP32 factors");
+            return FLYCOO_ERR_UNSUPPORTED;
+        }
+        switch (R) {
+        case 16: return launch_fused_t<N, 16, false, true>(a, s);
+        case 32: return launch_fused_t<N, 32, false, true>(a, s);
+        case 64: return launch_fused_t<N, 64, false, true>(a, s);
+        default: break;
+        }
+        set_error("rank %d not built (16, 32 or 64)", R);
+        return FLYCOO_ERR_UNSUPPORTED;
+    }
     switch (R) {
     case 16: return bf ? launch_fused_t<N, 16, true>(a, s) : launch_fused_t<N, 16, false>(a, s);
     case 32: return bf ? launch_fused_t<N, 32, true>(a, s) : launch_fused_t<N, 32, false>(a, s);

@@ -97,6 +97,7 @@ struct Tensor {
     u64 max_rows = 0;   // max over modes of min(m_n, I_n): rows of a super-shard
     DevBuf partials;    // max_S x max_rows x kMaxRank floats: one row block per shard
     DevBuf err;         // device error word: bit 0 = a bounded device wait gave up
+    DevBuf loss_part;   // bins doubles: per-block CP-OPT loss partials
     ModeMeta mode[FLYCOO_MAX_MODES];
     // kernel timing
     bool timing = false;
@@ -166,6 +167,8 @@ struct FusedArgs {
     const u32 *bin_ptr, *bin_items;
     float *partials;           // row block of shard s at s * m * R
     u32 *err;                  // device error word
+    const void *Yout;          // CP-OPT pass: the output mode's factor (nullptr: plain spMTTKRP)
+    double *loss_part;         // CP-OPT pass: per-block half sum of squared residuals (nullable)
     u32 I_out;
     u32 m;                     // super-shard width of the output mode
     u32 S;
