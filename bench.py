@@ -44,6 +44,7 @@ def parse_args(argv=None):
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-bf16", action="store_true")
+    ap.add_argument("--no-als", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=8_000_000, help="nonzeros in the CPU baseline sample")
     args = ap.parse_args(argv)
@@ -317,6 +318,25 @@ def main(argv=None):
         bf16 = {"ms_per_step": ms_b, "gbps": world * step_bb / (ms_b * 1e-3) / 1e9,
                 "speedup_vs_f32": step_ms / ms_b, "rel_fro_diff_vs_f32_gpu_per_mode": diff}
 
+    # ---- CP-ALS iterations (Algorithm 1 with the least-squares update) on the same tensor
+    als = None
+    if not args.no_als:
+        Ya = [y.clone() for y in Yf]
+        lam = torch.empty(R, dtype=torch.float64, device="cuda")
+        fits = [T.cp_als_step(Ya, lam)[1] for _ in range(2)]
+        torch.cuda.synchronize()
+        iters = max(3, min(args.steps, 10))
+        sa = torch.cuda.Event(enable_timing=True)
+        ea = torch.cuda.Event(enable_timing=True)
+        sa.record()
+        for _ in range(iters):
+            fits.append(T.cp_als_step(Ya, lam)[1])
+        ea.record()
+        ea.synchronize()
+        ms_a = reduce_max(sa.elapsed_time(ea) / iters, world)
+        als = {"ms_per_iter": ms_a, "iters_timed": iters, "spmttkrp_share": step_ms / ms_a,
+               "fits": fits, "factor_dtype": "f32"}
+
     # ---- end to end through the public API: pinned host factors in, outputs back out
     e2e = None
     if not args.no_e2e:
@@ -370,7 +390,7 @@ def main(argv=None):
                        "parallelism": "replicas" if world > 1 else "single"},
             "all_mode_ms": step_ms, "per_mode_ms": per_mode_ms, "bytes_per_step": step_b,
             "frac_of_hbm_peak": value / world / peak, "bf16": bf16, "preprocess_ms": create_s * 1e3,
-            "generate_s": gen_s, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "generate_s": gen_s, "cp_als": als, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches_per_step * args.steps, "clocks": clk,
         }
         print(json.dumps(line), flush=True)

@@ -15,8 +15,8 @@
  *    M_n is I_n x R in FP32.  Coordinates are 0-based (Section II-A).
  *  - Work is ordered on the given stream (a cudaStream_t; NULL is the legacy
  *    default stream).  Only flycoo_create, flycoo_sync, flycoo_cpopt_grad
- *    (for its loss), the export_* calls that fill host buffers and
- *    flycoo_timing_read wait for the stream.
+ *    (for its loss), flycoo_cp_als_step, the export_* calls that fill host
+ *    buffers and flycoo_timing_read wait for the stream.
  *  - Every entry point returns a flycoo_status and never aborts or traps;
  *    flycoo_last_error() then describes the failure (per calling thread).
  *  - A handle is not thread-safe: calls on one handle must not overlap.
@@ -198,6 +198,37 @@ flycoo_status flycoo_mttkrp_adjoint(flycoo_handle h, int mode, const float *cons
 /* ------------------------------------------------------------------------ */
 flycoo_status flycoo_cpopt_grad(flycoo_handle h, const float *const *h_factors, int R,
                                 float *const *h_grads, double *h_loss, flycoo_stream_t stream);
+
+/* ------------------------------------------------------------------------ */
+/* flycoo_cp_als_step -- one CP-ALS iteration (Algorithm 1, Section II-B).   */
+/* Modes are updated in order 0..N-1, each with the newest factors:          */
+/*   M_n = spMTTKRP_n(X, Y)                 (one fused pass, remapping on)   */
+/*   V   = hadamard_{w != n} Y_w^T Y_w      (R x R, FP64)                    */
+/*   Y_n = M_n V^{-1}                       (Cholesky of V in FP64)          */
+/*   lambda_r = ||Y_n[:, r]||_2,  Y_n[:, r] /= lambda_r  (0 norms kept as 1) */
+/* Algorithm 1 names the spMTTKRP and the normalisation; the least-squares   */
+/* solve between them is the standard CP-ALS update the paper builds on.     */
+/* The tensor is first remapped to L_0 if it is elsewhere; N passes later it */
+/* is back in L_0.  After the last mode                                      */
+/*   fit = 1 - ||X - Xhat||_F / ||X||_F,  Xhat = [[lambda; Y_0..Y_{N-1}]],  */
+/* from ||Xhat||^2 = lambda^T (hadamard_w Y_w^T Y_w) lambda and             */
+/* <X, Xhat> = sum_r lambda_r sum_i M_{N-1}[i,r] Y_{N-1}[i,r].               */
+/*  h_factors  HOST array of N DEVICE factor pointers (I_w x R, row-major,   */
+/*             type fdt, 16-byte aligned); updated in place                   */
+/*  fdt        FLYCOO_F32 or FLYCOO_BF16: the storage type of the factors;  */
+/*             an updated factor is rounded to FP32, then to BF16 (nearest  */
+/*             even) when stored in BF16, before later modes read it        */
+/*  R          16, 32 or 64                                                  */
+/*  d_lambda   DEVICE array of R doubles: the last mode's column norms       */
+/*  h_fit      HOST double, or NULL                                          */
+/* Waits for `stream`.  Allocates a workspace on the first call (about       */
+/* 2 x max_w I_w x 64 x 4 bytes), kept until flycoo_destroy.  Errors:        */
+/* INVALID_ARG (NULL or misaligned pointers, a tensor whose values are all  */
+/* zero), UNSUPPORTED (rank), NOT_SPD (a matrix V with a pivot <= 0: the     */
+/* modes before it were updated, the others are unchanged), OOM, CUDA.       */
+/* ------------------------------------------------------------------------ */
+flycoo_status flycoo_cp_als_step(flycoo_handle h, void *const *h_factors, flycoo_dtype fdt, int R,
+                                 double *d_lambda, double *h_fit, flycoo_stream_t stream);
 
 /* ------------------------------------------------------------------------ */
 /* flycoo_remap -- dynamic tensor remapping alone (Section III-B): move the  */

@@ -8,6 +8,7 @@ from ._native import (  # noqa: F401
     BF16,
     F32,
     FlycooError,
+    flycoo_cp_als_step,
     flycoo_cpopt_grad,
     flycoo_create,
     flycoo_destroy,

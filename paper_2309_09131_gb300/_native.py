@@ -67,6 +67,7 @@ def lib():
             "flycoo_sync": [P, P],
             "flycoo_mttkrp_adjoint": [P, I, P, I, P, P, P],
             "flycoo_cpopt_grad": [P, P, I, P, P, P],
+            "flycoo_cp_als_step": [P, P, I, I, P, P, P],
             "flycoo_get_info": [P, P],
             "flycoo_export_layout": [P, P, P, P],
             "flycoo_export_partition": [P, I, P, P, P],
@@ -233,6 +234,24 @@ def flycoo_cpopt_grad(h, factors: Sequence[torch.Tensor], grads: Sequence[torch.
     _check(lib().flycoo_cpopt_grad(h, F, int(R), Gr, ctypes.byref(loss) if want_loss else None,
                                    _stream(stream)))
     return loss.value if want_loss else None
+
+
+def flycoo_cp_als_step(h, factors: Sequence[torch.Tensor], lam: torch.Tensor, stream=None) -> float:
+    """One CP-ALS iteration: updates ``factors`` (all FP32 or all BF16) in
+    place, writes the last mode's column norms to ``lam`` (R float64 on the
+    device) and returns the fit."""
+    R = factors[0].shape[1]
+    dt = factors[0].dtype
+    if dt not in (torch.float32, torch.bfloat16) or any(f.dtype != dt for f in factors):
+        raise TypeError("factors must all be float32 or all bfloat16")
+    F = _ptr_array(factors, (dt,), "factor")
+    Lp = _dev_ptr(lam, (torch.float64,), "lambda")
+    if lam.numel() < R:
+        raise ValueError(f"lambda holds {lam.numel()} values, R = {R}")
+    fit = ctypes.c_double()
+    _check(lib().flycoo_cp_als_step(h, F, BF16 if dt == torch.bfloat16 else F32, int(R), Lp, ctypes.byref(fit),
+                                    _stream(stream)))
+    return fit.value
 
 
 def flycoo_remap(h, next_mode: int, stream=None) -> None:

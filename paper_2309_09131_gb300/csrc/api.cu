@@ -27,7 +27,7 @@ void set_error(const char *fmt, ...) {
 void clear_error() { g_last_error.clear(); }
 
 u64 Tensor::device_bytes() const {
-    u64 b = elem[0].bytes + elem[1].bytes + partials.bytes;
+    u64 b = elem[0].bytes + elem[1].bytes + partials.bytes + err.bytes + loss_part.bytes + als.bytes();
     for (int n = 0; n < N; ++n) {
         const ModeMeta &m = mode[n];
         b += m.d_shard_ptr.bytes + m.d_shard_ss.bytes + m.d_ss_shard_ptr.bytes + m.d_bin_ptr.bytes +
@@ -375,8 +375,8 @@ extern "C" flycoo_status flycoo_sync(flycoo_handle h, flycoo_stream_t stream) {
 
 // One fused pass of mode `mode` in its layout: spMTTKRP (Yout == nullptr) or the
 // CP-OPT gradient pass; fused remap to the next layout; then K4.
-static flycoo_status run_pass(Tensor &t, int mode, const void *const *F, flycoo_dtype fdt, int R, float *d_out,
-                              const void *Yout, double *loss_part, cudaStream_t s) {
+flycoo_status flycoo::run_pass(Tensor &t, int mode, const void *const *F, flycoo_dtype fdt, int R, float *d_out,
+                               const void *Yout, double *loss_part, cudaStream_t s) {
     const ModeMeta &md = t.mode[mode];
     if (t.nnz == 0) {
         FLY_TRY_CUDA(cudaMemsetAsync(d_out, 0, (size_t)t.dims[mode] * R * sizeof(float), s));
@@ -417,7 +417,7 @@ static flycoo_status run_pass(Tensor &t, int mode, const void *const *F, flycoo_
     return FLYCOO_OK;
 }
 
-static flycoo_status check_fp32_factors(const Tensor &t, const void *const *F, int skip, int R, const char *who) {
+static flycoo_status check_factor_ptrs(const Tensor &t, const void *const *F, int skip, int R, const char *who) {
     if (R != 16 && R != 32 && R != 64) {
         set_error("%s: rank %d not built (16, 32 or 64)", who, R);
         return R > 0 ? FLYCOO_ERR_UNSUPPORTED : FLYCOO_ERR_INVALID_ARG;
@@ -445,7 +445,7 @@ extern "C" flycoo_status flycoo_mttkrp_adjoint(flycoo_handle h, int mode, const 
         return FLYCOO_ERR_INVALID_ARG;
     }
     Tensor &t = *h;
-    FLY_TRY(check_fp32_factors(t, reinterpret_cast<const void *const *>(h_factors), mode, R, "flycoo_mttkrp_adjoint"));
+    FLY_TRY(check_factor_ptrs(t, reinterpret_cast<const void *const *>(h_factors), mode, R, "flycoo_mttkrp_adjoint"));
     if (!d_gout || (reinterpret_cast<uintptr_t>(d_gout) & 15u) || !h_gfactors) {
         set_error("flycoo_mttkrp_adjoint: d_gout / h_gfactors NULL or d_gout not 16-byte aligned");
         return FLYCOO_ERR_INVALID_ARG;
@@ -487,7 +487,7 @@ extern "C" flycoo_status flycoo_cpopt_grad(flycoo_handle h, const float *const *
         return FLYCOO_ERR_INVALID_ARG;
     }
     Tensor &t = *h;
-    FLY_TRY(check_fp32_factors(t, reinterpret_cast<const void *const *>(h_factors), -1, R, "flycoo_cpopt_grad"));
+    FLY_TRY(check_factor_ptrs(t, reinterpret_cast<const void *const *>(h_factors), -1, R, "flycoo_cpopt_grad"));
     if (!h_grads) {
         set_error("flycoo_cpopt_grad: h_grads is NULL");
         return FLYCOO_ERR_INVALID_ARG;
@@ -517,6 +517,27 @@ extern "C" flycoo_status flycoo_cpopt_grad(flycoo_handle h, const float *const *
         *h_loss = L;
     }
     return FLYCOO_OK;
+}
+
+extern "C" flycoo_status flycoo_cp_als_step(flycoo_handle h, void *const *h_factors, flycoo_dtype fdt, int R,
+                                            double *d_lambda, double *h_fit, flycoo_stream_t stream) {
+    clear_error();
+    if (!h) {
+        set_error("flycoo_cp_als_step: handle is NULL");
+        return FLYCOO_ERR_INVALID_ARG;
+    }
+    Tensor &t = *h;
+    if (fdt != FLYCOO_F32 && fdt != FLYCOO_BF16) {
+        set_error("flycoo_cp_als_step: unknown factor dtype %d", (int)fdt);
+        return FLYCOO_ERR_INVALID_ARG;
+    }
+    FLY_TRY(check_factor_ptrs(t, reinterpret_cast<const void *const *>(h_factors), -1, R, "flycoo_cp_als_step"));
+    if (!d_lambda) {
+        set_error("flycoo_cp_als_step: d_lambda is NULL");
+        return FLYCOO_ERR_INVALID_ARG;
+    }
+    DeviceGuard dg(t.device);
+    return als_step(t, h_factors, fdt, R, d_lambda, h_fit, reinterpret_cast<cudaStream_t>(stream));
 }
 
 extern "C" flycoo_status flycoo_remap(flycoo_handle h, int next_mode, flycoo_stream_t stream) {

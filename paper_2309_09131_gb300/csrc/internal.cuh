@@ -81,6 +81,25 @@ struct ModeMeta {
     DevBuf d_shard_ptr, d_shard_ss, d_ss_shard_ptr, d_bin_ptr, d_items, d_k4, d_next;
 };
 
+// CP-ALS workspace (als.cu), allocated by the first flycoo_cp_als_step
+struct AlsWork {
+    DevBuf M;       // max_n I_n x kMaxRank FP32: spMTTKRP of the mode being updated
+    DevBuf Y;       // max_n I_n x kMaxRank FP32: M V^{-1} before normalisation
+    DevBuf G;       // N x R x R FP64 Gram matrices of the stored factors
+    DevBuf gpart;   // per-block Gram partials
+    DevBuf W;       // R x R FP32 inverse of the normal-equation matrix
+    DevBuf colsq;   // per-block column sums of squares
+    DevBuf inner;   // per-block partials of <X, Xhat>
+    DevBuf scal;    // small FP64 results (||X||^2, fit) and the status word
+    u64 rows = 0;
+    int nblk = 0;
+    bool normx2_valid = false;
+    double normx2 = 0.0;
+    u64 bytes() const {
+        return M.bytes + Y.bytes + G.bytes + gpart.bytes + W.bytes + colsq.bytes + inner.bytes + scal.bytes;
+    }
+};
+
 struct Tensor {
     int N = 0;
     int device = 0;
@@ -98,6 +117,7 @@ struct Tensor {
     DevBuf partials;    // max_S x max_rows x kMaxRank floats: one row block per shard
     DevBuf err;         // device error word: bit 0 = a bounded device wait gave up
     DevBuf loss_part;   // bins doubles: per-block CP-OPT loss partials
+    AlsWork als;
     ModeMeta mode[FLYCOO_MAX_MODES];
     // kernel timing
     bool timing = false;
@@ -186,6 +206,13 @@ struct FixupArgs {
 };
 
 flycoo_status launch_fused(int N, int R, flycoo_dtype dt, const FusedArgs &a, cudaStream_t s);
+// one fused pass of `mode` in its layout (K2 + K4), leaving the tensor in L_{mode+1}:
+// spMTTKRP into d_out, or with Yout set the CP-OPT gradient pass (api.cu)
+flycoo_status run_pass(Tensor &t, int mode, const void *const *F, flycoo_dtype fdt, int R, float *d_out,
+                       const void *Yout, double *loss_part, cudaStream_t s);
+// K7/K8: one CP-ALS iteration, modes 0..N-1, from layout L_0 (als.cu)
+flycoo_status als_step(Tensor &t, void *const *F, flycoo_dtype fdt, int R, double *d_lambda, double *h_fit,
+                       cudaStream_t s);
 flycoo_status launch_fixup(int R, const FixupArgs &a, cudaStream_t s);
 bool fused_supported(int N, int R, flycoo_dtype dt);
 

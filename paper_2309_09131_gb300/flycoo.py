@@ -86,6 +86,28 @@ class FlycooTensor:
             nat.flycoo_spmttkrp(self.h, n, factors, outs[n], (n + 1) % self.N, stream)
         return outs
 
+    def cp_als_step(self, factors: Sequence[torch.Tensor], lam: Optional[torch.Tensor] = None,
+                    stream=None):
+        """One CP-ALS iteration (Algorithm 1 with the least-squares update),
+        factors updated in place; returns ``(lambda, fit)``."""
+        R = factors[0].shape[1]
+        if lam is None:
+            lam = torch.empty(R, dtype=torch.float64, device=factors[0].device)
+        fit = nat.flycoo_cp_als_step(self.h, factors, lam, stream)
+        return lam, fit
+
+    def cp_als(self, factors: Sequence[torch.Tensor], iters: int, tol: float = 0.0, stream=None):
+        """CP-ALS iterations until ``iters`` are done or the fit changes by
+        less than ``tol``; returns ``(lambda, fits)``."""
+        fits: List[float] = []
+        lam = None
+        for _ in range(iters):
+            lam, fit = self.cp_als_step(factors, lam, stream)
+            fits.append(fit)
+            if len(fits) > 1 and abs(fits[-1] - fits[-2]) < tol:
+                break
+        return lam, fits
+
     def remap(self, next_mode: int, stream=None) -> None:
         nat.flycoo_remap(self.h, next_mode, stream)
 

@@ -1,0 +1,232 @@
+"""GPU parity of one CP-ALS iteration (Algorithm 1 with the least-squares
+update, ``flycoo_cp_als_step``) against the FP64 oracle ``cp.cp_als_step``
+with the same storage rounding, plus properties that fix the result
+independently of the oracle: exact recovery of a planted dense CP tensor,
+monotone fit, the NOT_SPD status, determinism and the layout cycle.
+
+Tolerances.  The update solves Y_n = M_n V_n^{-1}; a relative error e in
+M_n (the spMTTKRP bar is 1e-5 in FP32) reaches Y_n amplified by at most the
+condition number kappa(V_n), and the N Gauss-Seidel updates add up, so FP32
+factors and lambda are held to 1e-5 * N * max_n kappa(V_n).  The fit moves
+by at most that relative error of the three terms of the squared residual,
+divided by d(resid^2)/d(fit) = 2 resid ||X||.  BF16 storage is held to the
+BF16 bar of 1e-2."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import cp
+from synth import make_coo, make_factors, random_coo
+
+from _util import rel_fro, to_np
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2309_09131_gb300 as pkg
+    pkg._native.lib()
+    return pkg
+
+
+def _kappa_max(old, new):
+    """max_n cond(V_n), V_n built as the Gauss-Seidel sweep sees it."""
+    N = len(old)
+    k = 1.0
+    for n in range(N):
+        V = np.ones((old[0].shape[1],) * 2)
+        for w in range(N):
+            if w != n:
+                y = new[w] if w < n else old[w]
+                V *= y.T @ y
+        k = max(k, float(np.linalg.cond(V)))
+    return k
+
+
+def _fit_tol(vals, Y, lam, M_last_inner, rel):
+    normx2 = float(np.dot(vals.astype(np.float64), vals.astype(np.float64)))
+    V = np.ones((lam.size, lam.size))
+    for y in Y:
+        V *= y.T @ y
+    xh2 = float(lam @ V @ lam)
+    resid2 = max(normx2 + xh2 - 2 * M_last_inner, 1e-300)
+    return rel * (normx2 + xh2 + 2 * abs(M_last_inner)) / (2 * math.sqrt(resid2) * math.sqrt(normx2))
+
+
+def _run_case(P, idx, vals, dims, facs, store, **kw):
+    N = len(dims)
+    R = facs[0].shape[1]
+    T = P.FlycooTensor(idx, vals, dims, **kw)
+    dt = torch.bfloat16 if store == "bf16" else torch.float32
+    Y = [torch.from_numpy(f).cuda().to(dt).contiguous() for f in facs]
+    start = [to_np(y.float()).astype(np.float64) for y in Y]
+    lam, fit = T.cp_als_step(Y)
+    torch.cuda.synchronize()
+    assert T.layout_mode == 0
+    Yo, lamo, fito = cp.cp_als_step(idx, vals, dims, start, store=store)
+    got = [to_np(y.float()).astype(np.float64) for y in Y]
+    return T, Y, got, to_np(lam), fit, start, Yo, lamo, fito
+
+
+@pytest.mark.parametrize("dims,nnz,R,law,g,bins", [
+    ((300, 200, 250), 40_000, 16, "zipf", 1000, 41),
+    ((300, 200, 250), 40_000, 32, "uniform", 700, 64),
+    ((500, 400, 300), 60_000, 64, "zipf", 2048, 97),
+    ((40, 50, 30, 20), 20_000, 32, "zipf", 600, 29),
+    ((30, 20, 25, 10, 12), 15_000, 16, "uniform", 333, 13),
+])
+def test_als_step_fp32_matches_oracle(P, dims, nnz, R, law, g, bins):
+    N = len(dims)
+    idx, vals = random_coo(dims, nnz, seed=11, law=law, value_law="lognormal")
+    facs = make_factors(dims, R, "normal", seed=11)
+    T, Y, got, lam, fit, start, Yo, lamo, fito = _run_case(P, idx, vals, dims, facs, "f32", g=g, bins=bins)
+    tol = 1e-5 * N * _kappa_max(start, Yo)
+    for n in range(N):
+        assert rel_fro(got[n], Yo[n]) <= tol, (n, rel_fro(got[n], Yo[n]), tol)
+    assert rel_fro(lam, lamo) <= tol
+    inner = float(lamo @ np.sum(oracle.mttkrp(idx, vals, Yo, N - 1, dims) * Yo[N - 1], axis=0))
+    assert abs(fit - fito) <= _fit_tol(vals, Yo, lamo, inner, tol) + 1e-12, (fit, fito)
+    # columns of every updated factor have unit 2-norm
+    for n in range(N):
+        np.testing.assert_allclose(np.linalg.norm(got[n], axis=0), 1.0, rtol=1e-5)
+
+
+@pytest.mark.parametrize("dims,nnz,R", [((300, 200, 250), 40_000, 32), ((40, 50, 30, 20), 20_000, 16)])
+def test_als_step_bf16_matches_oracle(P, dims, nnz, R):
+    idx, vals = random_coo(dims, nnz, seed=12, law="zipf", value_law="normal")
+    facs = make_factors(dims, R, "normal_over_sqrt_r", seed=12)
+    T, Y, got, lam, fit, start, Yo, lamo, fito = _run_case(P, idx, vals, dims, facs, "bf16", g=800, bins=37)
+    assert all(y.dtype == torch.bfloat16 for y in Y)
+    for n in range(len(dims)):
+        assert rel_fro(got[n], Yo[n]) <= 1e-2, (n, rel_fro(got[n], Yo[n]))
+    assert rel_fro(lam, lamo) <= 1e-2
+    assert fit == pytest.approx(fito, abs=1e-2)
+
+
+def test_als_step_skewed_rank64_sample(P):
+    # the 20K x 200K x 500K shape with a hot first mode (10 ids take half of
+    # the draws), R = 64, at 2M nonzeros: one step against the oracle
+    dims = (20_000, 200_000, 500_000)
+    idx, vals = make_coo(dims, 2_000_000, (("hot", 10, 0.5), ("uniform",), ("uniform",)), "normal", seed=5)
+    facs = make_factors(dims, 64, "normal_over_sqrt_r", seed=5)
+    T, Y, got, lam, fit, start, Yo, lamo, fito = _run_case(P, idx, vals, dims, facs, "f32")
+    tol = 1e-5 * 3 * _kappa_max(start, Yo)
+    for n in range(3):
+        assert rel_fro(got[n], Yo[n]) <= tol, (n, rel_fro(got[n], Yo[n]), tol)
+    assert rel_fro(lam, lamo) <= tol
+    inner = float(lamo @ np.sum(oracle.mttkrp(idx, vals, Yo, 2, dims) * Yo[2], axis=0))
+    assert abs(fit - fito) <= _fit_tol(vals, Yo, lamo, inner, tol) + 1e-12
+
+
+def _dense_model(Y, lam):
+    R = Y[0].shape[1]
+    X = np.zeros([y.shape[0] for y in Y])
+    for r in range(R):
+        t = lam[r]
+        for y in Y:
+            t = np.multiply.outer(t, y[:, r])
+        X += t
+    return X
+
+
+def test_als_recovers_planted_dense_cp_tensor(P):
+    # a dense tensor of exact rank 16 held as 24000 "nonzeros": ALS started
+    # near the generating factors converges to it (fit -> 1); the residual is
+    # recomputed here from the returned factors, independently of the fit
+    dims = (30, 40, 20)
+    R = 16
+    rng = np.random.default_rng(21)
+    Yt = [rng.standard_normal((d, R)) for d in dims]
+    X = _dense_model(Yt, np.ones(R))
+    idx = np.stack(np.meshgrid(*[np.arange(d) for d in dims], indexing="ij"), 0).reshape(3, -1).astype(np.uint32)
+    vals = X.reshape(-1).astype(np.float32)
+    T = P.FlycooTensor(idx, vals, dims, g=512, bins=23)
+    Y = [torch.from_numpy((y + 0.05 * rng.standard_normal(y.shape)).astype(np.float32)).cuda() for y in Yt]
+    lam, fits = T.cp_als(Y, iters=25)
+    # near fit 1 the fit formula cancels: ||X - Xhat||^2 is a difference of
+    # terms near ||X||^2, each carrying ~1e-6 relative error, so allow 2e-3
+    assert all(b >= a - 2e-3 for a, b in zip(fits, fits[1:])), fits
+    Xh = _dense_model([to_np(y).astype(np.float64) for y in Y], to_np(lam))
+    rel_resid = np.linalg.norm(Xh - vals.reshape(dims)) / np.linalg.norm(vals)
+    assert rel_resid < 1e-3, rel_resid
+    assert fits[-1] == pytest.approx(1.0 - rel_resid, abs=2e-3)
+
+
+def test_als_fit_monotone_on_sparse_data(P):
+    dims = (200, 150, 100)
+    idx, vals = random_coo(dims, 30_000, seed=13, law="zipf", value_law="int1to5")
+    facs = make_factors(dims, 16, "normal", seed=13)
+    T = P.FlycooTensor(idx, vals, dims, g=600, bins=31)
+    Y = [torch.from_numpy(f).cuda() for f in facs]
+    _, fits = T.cp_als(Y, iters=12)
+    # each mode update is an exact least-squares minimiser, so the fit of the
+    # sweep never drops (beyond the rounding of the fit formula)
+    assert all(b >= a - 1e-5 for a, b in zip(fits, fits[1:])), fits
+    assert fits[-1] > fits[0]
+
+
+def test_als_step_deterministic_and_layout_cycle(P):
+    dims = (120, 90, 70)
+    idx, vals = random_coo(dims, 15_000, seed=14, law="zipf")
+    facs = make_factors(dims, 32, "normal", seed=14)
+    out = []
+    for start_layout in (0, 2):
+        T = P.FlycooTensor(idx, vals, dims, g=400, bins=19)
+        if start_layout:
+            T.remap(start_layout)
+        Y = [torch.from_numpy(f).cuda() for f in facs]
+        lam, fit = T.cp_als_step(Y)
+        assert T.layout_mode == 0
+        out.append(([to_np(y) for y in Y], to_np(lam), fit))
+    (Ya, la, fa), (Yb, lb, fb) = out
+    assert fa == fb
+    np.testing.assert_array_equal(la, lb)
+    for a, b in zip(Ya, Yb):
+        np.testing.assert_array_equal(a, b)
+
+
+def test_als_not_spd_status(P):
+    # a zero column in Y_1 makes V_0 = G_1 * G_2 singular (V_0[0,0] = 0): the
+    # oracle raises NotSPD and the library returns NOT_SPD, leaving every
+    # factor unchanged (mode 0 is the first update)
+    dims = (50, 40, 30)
+    idx, vals = random_coo(dims, 5_000, seed=15)
+    facs = make_factors(dims, 16, "normal", seed=15)
+    facs[1][:, 0] = 0.0
+    with pytest.raises(cp.NotSPD):
+        cp.cp_als_step(idx, vals, dims, [f.astype(np.float64) for f in facs])
+    T = P.FlycooTensor(idx, vals, dims, g=256, bins=7)
+    Y = [torch.from_numpy(f).cuda() for f in facs]
+    with pytest.raises(P.FlycooError) as ei:
+        T.cp_als_step(Y)
+    assert ei.value.status_name == "FLYCOO_ERR_NOT_SPD"
+    assert "positive definite" in P.flycoo_last_error()
+    for y, f in zip(Y, facs):
+        np.testing.assert_array_equal(to_np(y), f)
+    assert T.layout_mode == 0
+    # the handle stays usable
+    Y[1][:, 0] = 1.0
+    T.cp_als_step(Y)
+
+
+def test_als_argument_errors(P):
+    dims = (20, 20, 20)
+    idx, vals = random_coo(dims, 1_000, seed=16)
+    T = P.FlycooTensor(idx, vals, dims, g=128, bins=3)
+    Y = [torch.randn(d, 16, device="cuda") for d in dims]
+    with pytest.raises(TypeError):
+        T.cp_als_step([Y[0], Y[1].bfloat16(), Y[2]])
+    Y24 = [torch.randn(d, 24, device="cuda") for d in dims]
+    with pytest.raises(P.FlycooError) as ei:
+        T.cp_als_step(Y24)
+    assert ei.value.status_name == "FLYCOO_ERR_UNSUPPORTED"
+    zero = P.FlycooTensor(idx, np.zeros_like(vals), dims, g=128, bins=3)
+    with pytest.raises(P.FlycooError) as ei:
+        zero.cp_als_step(Y)
+    assert ei.value.status_name == "FLYCOO_ERR_INVALID_ARG"
