@@ -204,7 +204,7 @@ flycoo_status flycoo_cpopt_grad(flycoo_handle h, const float *const *h_factors, 
 /* Modes are updated in order 0..N-1, each with the newest factors:          */
 /*   M_n = spMTTKRP_n(X, Y)                 (one fused pass, remapping on)   */
 /*   V   = hadamard_{w != n} Y_w^T Y_w      (R x R, FP64)                    */
-/*   Y_n = M_n V^{-1}                       (Cholesky of V in FP64)          */
+/*   Y_n = M_n V^{-1}                       (V = L D L^T in FP64)            */
 /*   lambda_r = ||Y_n[:, r]||_2,  Y_n[:, r] /= lambda_r  (0 norms kept as 1) */
 /* Algorithm 1 names the spMTTKRP and the normalisation; the least-squares   */
 /* solve between them is the standard CP-ALS update the paper builds on.     */

@@ -6,8 +6,9 @@
 // 0..N-1 (Gauss-Seidel, each update sees the newest factors):
 //   1. M_n: one fused spMTTKRP + remap pass (K2 + K4), L_n -> L_{n+1};
 //   2. V = hadamard_{w != n} G_w in FP64 (R x R);
-//   3. Cholesky V = L L^T and W = V^{-1} in FP64, one block; a pivot that is
-//      not positive ends the step with FLYCOO_ERR_NOT_SPD;
+//   3. V = L D L^T and W = V^{-1} in FP64 (R/8 blocks, one column of W per
+//      warp); a pivot that is not positive ends the step with
+//      FLYCOO_ERR_NOT_SPD;
 //   4. Y = M_n W in FP32 (W rounded to FP32) and the column sums of squares;
 //   5. lambda_r = column 2-norm (FP64); Y_n = Y / lambda rounded to FP32, then
 //      to BF16 when the factors are stored in BF16;
@@ -90,23 +91,57 @@ __global__ void __launch_bounds__(kAlsThreads) gram_partial_kernel(const void *Y
         for (int y = 0; y < B; ++y) o[(a0 + x) * R + c0 + y] = acc[x][y];
 }
 
-// out[e] = sum_b partials[b][e], blocks in order
-__global__ void sum_partials_kernel(const double *partials, int nblocks, int len, double *out) {
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < len; e += gridDim.x * blockDim.x) {
-        double s = 0.0;
-        for (int b = 0; b < nblocks; ++b) s += partials[(size_t)b * len + e];
-        out[e] = s;
+// out[e] = sum over b < nblocks of partials[b * len + e] (sqrt of it with
+// take_sqrt), in a fixed order: warp q of a block sums b = q, q + 8, ... for 32
+// consecutive e, then the 8 warp sums are added in warp order.  Skipped when
+// *status is set.
+__global__ void __launch_bounds__(256) reduce_partials_kernel(const double *partials, int nblocks, int len,
+                                                              double *out, int take_sqrt, const u32 *status) {
+    __shared__ double part[8][32];
+    if (status && *status) return;
+    const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
+    const int e = blockIdx.x * 32 + lane;
+    double s = 0.0;
+    if (e < len)
+        for (int b = wq; b < nblocks; b += 8) s += partials[(size_t)b * len + e];
+    part[wq][lane] = s;
+    __syncthreads();
+    if (wq == 0 && e < len) {
+        double t = 0.0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) t += part[q][lane];
+        out[e] = take_sqrt ? sqrt(t) : t;
     }
 }
 
-// V = hadamard_{w != n} G_w; V = L L^T (lower triangle of V overwritten by L);
-// W = V^{-1} by one forward and one backward substitution per column of I.
-// One block, 2 R^2 doubles of dynamic shared memory.  *status = 1 when a pivot
-// is not positive.
-__global__ void __launch_bounds__(kAlsThreads)
-    chol_inverse_kernel(const double *G, int N, int n, int R, float *W, u32 *status) {
-    extern __shared__ double chol_smem[];
-    double *V = chol_smem, *Z = chol_smem + R * R;
+// FP64 is a narrow pipe on this GPU, so a serial chain of FP64 divisions is
+// slow.  1/d: an FP32 estimate refined by two Newton-Raphson steps
+// r <- r + r (1 - d r); each step squares the relative error (2^-23 -> 2^-46
+// -> FP64 rounding).  Outside the range where the FP32 estimate is accurate the
+// plain division is used.
+__device__ __forceinline__ double recip_f64(double d) {
+    if (!(d > 1e-30 && d < 1e30)) return 1.0 / d;
+    double r = (double)__frcp_rn((float)d);
+    double e = fma(-d, r, 1.0);
+    r = fma(r, e, r);
+    e = fma(-d, r, 1.0);
+    return fma(r, e, r);
+}
+
+constexpr int kInvWarps = 8; // columns of the inverse per block, one per warp
+
+// W = V^{-1} for V = hadamard_{w != n} G_w (R x R, symmetric), in FP64, by the
+// factorisation V = L D L^T (L unit lower triangular, D diagonal): a
+// positive-definite V has every pivot d_k > 0, and a pivot <= 0 sets *status.
+// Each block factors V itself (R^3/6 FMAs) and then solves kInvWarps columns
+// c of W, one per warp, lanes owning rows i = lane and lane + 32:
+//   L z = e_c,   y = D^{-1} z,   L^T w = y,   W[:, c] = w.
+// Shared memory: V (R x R) and the pivot reciprocals (R).  After the loop the
+// strictly lower triangle of V holds L and the strictly upper one L^T.
+__global__ void __launch_bounds__(kInvWarps * 32)
+    ldl_inverse_kernel(const double *G, int N, int n, int R, float *W, u32 *status) {
+    extern __shared__ double inv_smem[];
+    double *V = inv_smem, *dinv = inv_smem + R * R;
     __shared__ int bad;
     if (*status) return; // an earlier mode failed: leave the rest untouched
     const int RR = R * R;
@@ -122,38 +157,54 @@ __global__ void __launch_bounds__(kAlsThreads)
         if (threadIdx.x == 0) {
             const double d = V[k * R + k];
             if (!(d > 0.0)) bad = 1;
-            else V[k * R + k] = sqrt(d);
+            else dinv[k] = recip_f64(d);
         }
         __syncthreads();
         if (bad) break;
-        const double lkk = V[k * R + k];
-        for (int i = k + 1 + threadIdx.x; i < R; i += blockDim.x) V[i * R + k] /= lkk;
-        __syncthreads();
-        // trailing update of the lower triangle: V[i][j] -= L[i][k] L[j][k], k < j <= i
-        for (int e = threadIdx.x; e < RR; e += blockDim.x) {
-            const int i = e / R, j = e % R;
-            if (j > k && i >= j) V[i * R + j] -= V[i * R + k] * V[j * R + k];
+        const double r = dinv[k];
+        // rows i > k: V[i][j] -= V[i][k] L[j][k] for k < j <= i, with
+        // L[j][k] = V[j][k] / d_k, and L[i][k] stored at V[k][i] (upper); the
+        // update reads column k below the diagonal and writes neither it nor row k
+        const int t = R - k - 1;
+        for (int e = threadIdx.x; e < t * t; e += blockDim.x) {
+            const int i = k + 1 + e / t, j = k + 1 + e % t;
+            if (j <= i) V[i * R + j] -= V[i * R + k] * (V[j * R + k] * r);
         }
+        for (int i = k + 1 + threadIdx.x; i < R; i += blockDim.x) V[k * R + i] = V[i * R + k] * r;
         __syncthreads();
     }
     if (bad) {
-        if (threadIdx.x == 0) *status = 1u;
+        if (threadIdx.x == 0 && blockIdx.x == 0) *status = 1u;
         return;
     }
-    for (int c = threadIdx.x; c < R; c += blockDim.x) {
-        for (int i = 0; i < R; ++i) { // L z = e_c
-            double s = (i == c) ? 1.0 : 0.0;
-            for (int q = 0; q < i; ++q) s -= V[i * R + q] * Z[q * R + c];
-            Z[i * R + c] = s / V[i * R + i];
-        }
-        for (int i = R - 1; i >= 0; --i) { // L^T w = z
-            double s = Z[i * R + c];
-            for (int q = i + 1; q < R; ++q) s -= V[q * R + i] * Z[q * R + c];
-            Z[i * R + c] = s / V[i * R + i];
-        }
+    // lower triangle: L[i][k] = V[k][i] (copy the scaled values down)
+    for (int e = threadIdx.x; e < RR; e += blockDim.x) {
+        const int i = e / R, k = e % R;
+        if (k < i) V[i * R + k] = V[k * R + i];
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < RR; e += blockDim.x) W[e] = (float)Z[e];
+    const int lane = threadIdx.x & 31;
+    const int c = blockIdx.x * kInvWarps + (threadIdx.x >> 5);
+    if (c >= R) return;
+    const int i0 = lane, i1 = lane + 32; // rows of this lane (R <= 64)
+    const bool has0 = i0 < R, has1 = i1 < R;
+    // forward: z_i -= L[i][q] z_q for i > q, q = c .. R-2 (z_q = 0 for q < c)
+    double z0 = (i0 == c) ? 1.0 : 0.0, z1 = (i1 == c) ? 1.0 : 0.0;
+    for (int q = c; q < R - 1; ++q) {
+        const double zq = __shfl_sync(0xffffffffu, q < 32 ? z0 : z1, q & 31);
+        if (has0 && i0 > q) z0 -= V[q * R + i0] * zq; // V[q][i] = L[i][q] (upper copy)
+        if (has1 && i1 > q) z1 -= V[q * R + i1] * zq;
+    }
+    if (has0) z0 *= dinv[i0];
+    if (has1) z1 *= dinv[i1];
+    // backward: w_i -= L[q][i] w_q for i < q, q = R-1 .. 1
+    for (int q = R - 1; q > 0; --q) {
+        const double wq = __shfl_sync(0xffffffffu, q < 32 ? z0 : z1, q & 31);
+        if (has0 && i0 < q) z0 -= V[q * R + i0] * wq; // V[q][i] = L[q][i] (lower)
+        if (has1 && i1 < q) z1 -= V[q * R + i1] * wq;
+    }
+    if (has0) W[i0 * R + c] = (float)z0;
+    if (has1) W[i1 * R + c] = (float)z1;
 }
 
 // Y = M W in FP32; thread t computes column c = t % R of rows lo + t/R, stepping
@@ -194,16 +245,8 @@ __global__ void __launch_bounds__(kAlsThreads)
     }
 }
 
-__global__ void norms_kernel(const double *colsq, int nblocks, int R, double *lambda, const u32 *status) {
-    const int r = threadIdx.x;
-    if (r >= R || *status) return;
-    double s = 0.0;
-    for (int b = 0; b < nblocks; ++b) s += colsq[(size_t)b * R + r];
-    lambda[r] = sqrt(s);
-}
-
-// factor = Y / lambda (FP64 divide, rounded to FP32, then to BF16 when stored
-// so); with M set, also the per-block partials of sum_i M[i,r] factor[i,r]
+// factor = Y * (1 / lambda) in FP64, rounded to FP32, then to BF16 when stored
+// so; with M set, also the per-block partials of sum_i M[i,r] factor[i,r]
 template <bool BF16>
 __global__ void __launch_bounds__(kAlsThreads)
     normalize_store_kernel(const float *Yt, const double *lambda, void *Yout, u64 I, int R, const float *M,
@@ -213,12 +256,12 @@ __global__ void __launch_bounds__(kAlsThreads)
     const int rstep = kAlsThreads / R;
     const int c = threadIdx.x % R, rsub = threadIdx.x / R;
     const double lam = lambda[c];
-    const double div = lam > 0.0 ? lam : 1.0;
+    const double inv = lam > 0.0 ? 1.0 / lam : 1.0;
     u64 lo, hi;
     block_rows(I, lo, hi);
     double s = 0.0;
     for (u64 i = lo + rsub; i < hi; i += rstep) {
-        float stored = (float)((double)Yt[i * R + c] / div);
+        float stored = (float)((double)Yt[i * R + c] * inv);
         if constexpr (BF16) {
             const __nv_bfloat16 b = __float2bfloat16_rn(stored);
             static_cast<__nv_bfloat16 *>(Yout)[i * R + c] = b;
@@ -239,6 +282,23 @@ __global__ void __launch_bounds__(kAlsThreads)
     }
 }
 
+// sum of part[0 .. kAlsThreads) in a fixed order: each warp adds its 8-value
+// strip serially, then thread 0 adds the 32 strip sums in order
+__device__ double block_sum_fixed(double *part) {
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double t = 0.0;
+#pragma unroll
+        for (int q = 0; q < kAlsThreads / 32; ++q) t += part[threadIdx.x * (kAlsThreads / 32) + q];
+        part[threadIdx.x * (kAlsThreads / 32)] = t;
+    }
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int q = 0; q < 32; ++q) t += part[q * (kAlsThreads / 32)];
+    return t; // valid in thread 0
+}
+
 // fit from ||X||^2, the Gram matrices, lambda and the <X, Xhat> partials.  One block.
 __global__ void __launch_bounds__(kAlsThreads) fit_kernel(const double *G, int N, int R, const double *lambda,
                                                           const double *inner, int nblocks, const double *normx2,
@@ -253,13 +313,9 @@ __global__ void __launch_bounds__(kAlsThreads) fit_kernel(const double *G, int N
     for (int e = threadIdx.x; e < nblocks * R; e += kAlsThreads) xi += lambda[e % R] * inner[e];
     part[0][threadIdx.x] = xh;
     part[1][threadIdx.x] = xi;
-    __syncthreads();
+    const double sxh = block_sum_fixed(part[0]);
+    const double sxi = block_sum_fixed(part[1]);
     if (threadIdx.x == 0) {
-        double sxh = 0.0, sxi = 0.0;
-        for (int q = 0; q < kAlsThreads; ++q) {
-            sxh += part[0][q];
-            sxi += part[1][q];
-        }
         const double x2 = *normx2;
         const double resid2 = fmax(x2 + sxh - 2.0 * sxi, 0.0);
         *fit = 1.0 - sqrt(resid2) / sqrt(x2);
@@ -278,12 +334,8 @@ __global__ void __launch_bounds__(kAlsThreads)
         s += v * v;
     }
     part[threadIdx.x] = s;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int q = 0; q < kAlsThreads; ++q) t += part[q];
-        partials[blockIdx.x] = t;
-    }
+    const double t = block_sum_fixed(part);
+    if (threadIdx.x == 0) partials[blockIdx.x] = t;
 }
 
 template <int R>
@@ -298,7 +350,7 @@ flycoo_status gram(const void *Y, bool bf16, u64 I, int R, double *G, double *gp
     case 32: launch_gram_t<32>(Y, bf16, I, gpart, nblk, s); break;
     default: launch_gram_t<64>(Y, bf16, I, gpart, nblk, s); break;
     }
-    sum_partials_kernel<<<(R * R + 255) / 256, 256, 0, s>>>(gpart, nblk, R * R, G);
+    reduce_partials_kernel<<<(R * R + 31) / 32, 256, 0, s>>>(gpart, nblk, R * R, G, 0, nullptr);
     FLY_TRY_CUDA(cudaGetLastError());
     return FLYCOO_OK;
 }
@@ -323,8 +375,6 @@ flycoo_status als_step(Tensor &t, void *const *F, flycoo_dtype fdt, int R, doubl
     for (int n = 0; n < N; ++n) maxI = std::max<u64>(maxI, t.dims[n]);
     const int nblk = 2 * t.sm_count;
     if (w.rows < maxI || w.nblk != nblk) {
-        FLY_TRY_CUDA(cudaFuncSetAttribute(chol_inverse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          2 * kMaxRank * kMaxRank * (int)sizeof(double)));
         FLY_TRY(w.M.alloc(maxI * kMaxRank * sizeof(float)));
         FLY_TRY(w.Y.alloc(maxI * kMaxRank * sizeof(float)));
         FLY_TRY(w.G.alloc((size_t)FLYCOO_MAX_MODES * kMaxRank * kMaxRank * sizeof(double)));
@@ -350,7 +400,7 @@ flycoo_status als_step(Tensor &t, void *const *F, flycoo_dtype fdt, int R, doubl
     if (!w.normx2_valid) {
         if (t.nnz) {
             value_sq_kernel<<<nblk, kAlsThreads, 0, s>>>(t.elem[t.cur].as<u32>(), t.elem_words, N, t.nnz, scal + 4);
-            sum_partials_kernel<<<1, 32, 0, s>>>(scal + 4, nblk, 1, scal);
+            reduce_partials_kernel<<<1, 256, 0, s>>>(scal + 4, nblk, 1, scal, 0, nullptr);
             FLY_TRY_CUDA(cudaGetLastError());
         } else {
             FLY_TRY_CUDA(cudaMemsetAsync(scal, 0, sizeof(double), s));
@@ -369,10 +419,11 @@ flycoo_status als_step(Tensor &t, void *const *F, flycoo_dtype fdt, int R, doubl
     for (int n = 0; n < N; ++n) {
         const u64 I = t.dims[n];
         FLY_TRY(run_pass(t, n, F, fdt, R, w.M.as<float>(), nullptr, nullptr, s));
-        chol_inverse_kernel<<<1, kAlsThreads, 2 * RR * sizeof(double), s>>>(G, N, n, R, w.W.as<float>(), status);
+        ldl_inverse_kernel<<<(R + kInvWarps - 1) / kInvWarps, kInvWarps * 32, (RR + R) * sizeof(double), s>>>(
+            G, N, n, R, w.W.as<float>(), status);
         launch_apply(R, w.M.as<float>(), w.W.as<float>(), w.Y.as<float>(), I, w.colsq.as<double>(), status, nblk,
                      s);
-        norms_kernel<<<1, kMaxRank, 0, s>>>(w.colsq.as<double>(), nblk, R, d_lambda, status);
+        reduce_partials_kernel<<<(R + 31) / 32, 256, 0, s>>>(w.colsq.as<double>(), nblk, R, d_lambda, 1, status);
         const bool last = n == N - 1;
         float *Mlast = last ? w.M.as<float>() : nullptr;
         double *inner = last ? w.inner.as<double>() : nullptr;
