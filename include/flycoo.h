@@ -150,9 +150,10 @@ flycoo_status flycoo_spmttkrp(flycoo_handle h, int mode, const void *const *h_fa
 /* of the call, for example code running while another allocator owns the    */
 /* GPU's free memory, or code that must not enter cudaMalloc on a time-bound  */
 /* path.  The handle itself still comes from flycoo_create, which allocates.  */
-/*  - Limit: 2 x S_mode x R x 4 bytes must fit in 8 MiB (S_mode = shards of    */
-/*    the mode, see flycoo_get_info); larger requests return INVALID_ARG and   */
-/*    flycoo_last_error() gives both sizes.  A larger g lowers S_mode.         */
+/*  - Limit: S_mode x m_mode x R x 4 bytes must fit in 8 MiB (S_mode = shards */
+/*    and m_mode = super-shard width of the mode, see flycoo_get_info);        */
+/*    larger requests return INVALID_ARG and flycoo_last_error() gives both    */
+/*    sizes.  A larger g lowers S_mode.                                        */
 /*  - The first call on a device looks up the array's device address with     */
 /*    that device current; make that first call before any stream capture.    */
 /*  - All calls on a device share the one array and it keeps the last call's  */

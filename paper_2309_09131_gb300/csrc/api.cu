@@ -31,7 +31,7 @@ u64 Tensor::device_bytes() const {
     for (int n = 0; n < N; ++n) {
         const ModeMeta &m = mode[n];
         b += m.d_shard_ptr.bytes + m.d_shard_ss.bytes + m.d_ss_shard_ptr.bytes + m.d_bin_ptr.bytes +
-             m.d_items.bytes + m.d_k4.bytes + m.d_next.bytes;
+             m.d_items.bytes + m.d_k4.bytes + m.d_next.bytes + m.d_tiles.bytes + m.d_tile_bin_ptr.bytes;
     }
     return b;
 }
@@ -118,6 +118,24 @@ flycoo_status partition_mode(Tensor &t, int n, const std::vector<u32> &ssp, cuda
     md.tile_ptr.push_back((u32)t.nnz);
     lpt_schedule(ss_shards, t.bins, md.ss_bin_ptr, md.ss_items);
     lpt_schedule(shard_size, t.bins, md.sh_bin_ptr, md.sh_items);
+    // tile descriptors of the block schedule
+    md.tiles.clear();
+    md.tile_bin_ptr.assign((size_t)t.bins + 1, 0);
+    for (u32 b = 0; b < t.bins; ++b) {
+        md.tile_bin_ptr[b] = (u32)(md.tiles.size() / 4);
+        for (u64 it = md.sh_bin_ptr[b]; it < md.sh_bin_ptr[b + 1]; ++it) {
+            const u32 sh = md.sh_items[it];
+            const u32 j = md.shard_ss[sh];
+            const u32 lo = md.shard_ptr[sh], hi = md.shard_ptr[sh + 1];
+            const u32 alone = ss_shards[j] == 1 ? 4u : 0u;
+            for (u32 p = lo; p < hi; p += kLayoutTile) {
+                const u32 len = std::min<u32>(kLayoutTile, hi - p);
+                const u32 flags = (p == lo ? 1u : 0u) | (p + len == hi ? 2u : 0u) | alone;
+                md.tiles.insert(md.tiles.end(), {p, len | (flags << 16), j, sh});
+            }
+        }
+    }
+    md.tile_bin_ptr[t.bins] = (u32)(md.tiles.size() / 4);
     // K4 writes the rows of every super-shard that does not have exactly one shard
     md.k4_items.clear();
     for (u64 j = 0; j < md.k; ++j)
@@ -128,6 +146,8 @@ flycoo_status partition_mode(Tensor &t, int n, const std::vector<u32> &ssp, cuda
     FLY_TRY(upload(md.d_bin_ptr, md.sh_bin_ptr, s));
     FLY_TRY(upload(md.d_items, md.sh_items, s));
     FLY_TRY(upload(md.d_k4, md.k4_items, s));
+    FLY_TRY(upload(md.d_tiles, md.tiles, s));
+    FLY_TRY(upload(md.d_tile_bin_ptr, md.tile_bin_ptr, s));
     return FLYCOO_OK;
 }
 
@@ -321,6 +341,8 @@ extern "C" flycoo_status flycoo_spmttkrp(flycoo_handle h, int mode, const void *
     a.ss_shard_ptr = md.d_ss_shard_ptr.as<u32>();
     a.bin_ptr = md.d_bin_ptr.as<u32>();
     a.bin_items = md.d_items.as<u32>();
+    a.tiles = md.d_tiles.as<uint4>();
+    a.tile_bin_ptr = md.d_tile_bin_ptr.as<u32>();
     a.partials = t.partials.as<float>();
     a.err = t.err.as<u32>();
     a.I_out = (u32)t.dims[mode];
@@ -394,6 +416,8 @@ flycoo_status flycoo::run_pass(Tensor &t, int mode, const void *const *F, flycoo
     a.ss_shard_ptr = md.d_ss_shard_ptr.as<u32>();
     a.bin_ptr = md.d_bin_ptr.as<u32>();
     a.bin_items = md.d_items.as<u32>();
+    a.tiles = md.d_tiles.as<uint4>();
+    a.tile_bin_ptr = md.d_tile_bin_ptr.as<u32>();
     a.partials = t.partials.as<float>();
     a.err = t.err.as<u32>();
     a.Yout = Yout;

@@ -42,6 +42,8 @@
 
 #include "internal.cuh"
 
+#include <type_traits>
+
 namespace flycoo {
 
 template <int N, int R, bool BF16>
@@ -55,7 +57,6 @@ struct FusedCfg {
     static constexpr int EW = (N + 1 <= 4) ? 4 : 8; // 32-bit words per stored nonzero
     static constexpr int EQ = EW / 4;               // 16-byte chunks per stored nonzero
     static constexpr int EB = EW * 4;               // bytes per stored nonzero
-    static constexpr int SUB = (N <= 3) ? FLYCOO_SUB3 : 1; // nonzeros whose gathers are in flight together
     static constexpr int M = (int)kMaxSuperShardRows;
     static constexpr int CAP = (int)kLayoutTile;    // one layout tile per stage
     // shared memory
@@ -165,33 +166,8 @@ __device__ __forceinline__ void store_zero(float *dst) {
     for (int q = 0; q < VEC / 4; ++q) reinterpret_cast<float4 *>(dst)[q] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
-// Walks a block's sequence of tiles: the shards of its bin, each cut into tiles.
-template <int CAP>
-struct TileCursor {
-    u32 it, it_end, s, start, len, shard_end;
-    __device__ void load_shard(const FusedArgs &a) {
-        s = a.bin_items[it];
-        start = a.shard_ptr[s];
-        shard_end = a.shard_ptr[s + 1];
-        len = min((u32)CAP, shard_end - start);
-    }
-    __device__ void begin(const FusedArgs &a, u32 b) {
-        it = a.bin_ptr[b];
-        it_end = a.bin_ptr[b + 1];
-        if (it < it_end) load_shard(a);
-    }
-    __device__ bool valid() const { return it < it_end; }
-    __device__ bool first_tile(const FusedArgs &a) const { return start == a.shard_ptr[s]; }
-    __device__ bool last_tile() const { return start + len == shard_end; }
-    __device__ void advance(const FusedArgs &a) {
-        if (start + len < shard_end) {
-            start += len;
-            len = min((u32)CAP, shard_end - start);
-        } else if (++it < it_end) {
-            load_shard(a);
-        }
-    }
-};
+// A tile descriptor: four words start, len | flags << 16, super-shard, shard.
+constexpr u32 kTileFirst = 1u, kTileLast = 2u, kTileAlone = 4u;
 
 template <int N, int R, bool BF16, bool CPOPT>
 __global__ void __launch_bounds__(256, kBlocksPerSM) fused_mttkrp_remap_kernel(const FusedArgs a) {
@@ -202,6 +178,8 @@ __global__ void __launch_bounds__(256, kBlocksPerSM) fused_mttkrp_remap_kernel(c
     constexpr int CAP = C::CAP;
     constexpr int G = C::G;
     constexpr int M = C::M;
+    constexpr int NF = CPOPT ? N : N - 1;            // factor rows gathered per nonzero
+    constexpr int U = (N == 3 && !CPOPT) ? (BF16 ? FLYCOO_UNROLL3 - 1 : FLYCOO_UNROLL3) : 2; // nonzeros per group per step
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float *acc = reinterpret_cast<float *>(smem_raw + 2 * C::STAGE);          // [M][R]
     float *hacc = acc + M * R;                                               // [G][R]
@@ -210,6 +188,7 @@ __global__ void __launch_bounds__(256, kBlocksPerSM) fused_mttkrp_remap_kernel(c
     u32 *trow = hrow + G;
     u32 *multi = trow + G;
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw + 2 * C::STAGE + C::ACC + C::SUMBUF);
+    uint4 *sdesc = reinterpret_cast<uint4 *>(bar + 2); // descriptor of the tile in each stage
 
     const int tid = threadIdx.x;
     const int lane = tid & 31;
@@ -227,7 +206,12 @@ __global__ void __launch_bounds__(256, kBlocksPerSM) fused_mttkrp_remap_kernel(c
     double loss = 0.0;
     float *my_hacc = hacc + grp * R + k * VEC;
     float *my_tacc = tacc + grp * R + k * VEC;
+    const u32 t_begin = a.tile_bin_ptr[blockIdx.x];
+    const u32 ntile = a.tile_bin_ptr[blockIdx.x + 1] - t_begin;
 
+    // the accumulator starts at zero; the flush at the end of every shard zeroes it again
+    for (u32 i = tid; i < (u32)(M * R / 4); i += C::THREADS)
+        reinterpret_cast<float4 *>(acc)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     if (tid == 0) {
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
@@ -235,46 +219,42 @@ __global__ void __launch_bounds__(256, kBlocksPerSM) fused_mttkrp_remap_kernel(c
     }
     __syncthreads();
 
-    TileCursor<CAP> cur, pre;
-    cur.begin(a, blockIdx.x);
-    pre = cur;
-    auto issue = [&](int st, const TileCursor<CAP> &c) {
+    // thread 0: load a tile (and its next-layout slots) into a stage.  The
+    // descriptor written to sdesc reaches the waiting threads through the
+    // release of the arrive and the acquire of their wait on the same barrier.
+    auto issue = [&](int st, const uint4 d) {
+        const u32 start = d.x, len = d.y & 0xffffu;
         unsigned char *sb = smem_raw + (size_t)st * C::STAGE;
-        const u32 nlo = c.start & ~3u;
-        const u32 nhi = (c.start + c.len + 3u) & ~3u;
-        u32 bytes = c.len * C::EB;
+        const u32 nlo = start & ~3u;
+        const u32 nhi = (start + len + 3u) & ~3u;
+        u32 bytes = len * C::EB;
         if (remap) bytes += (nhi - nlo) * 4u;
+        sdesc[st] = d;
         fence_proxy_async_smem();
         mbar_arrive_expect_tx(&bar[st], bytes);
-        tma_load_1d(sb, ein + (size_t)c.start * C::EQ, c.len * C::EB, &bar[st]);
+        tma_load_1d(sb, ein + (size_t)start * C::EQ, len * C::EB, &bar[st]);
         if (remap) tma_load_1d(sb + (size_t)CAP * C::EB, a.next + nlo, (nhi - nlo) * 4u, &bar[st]);
     };
-    if (tid == 0 && pre.valid()) {
-        issue(0, pre);
-        pre.advance(a);
-        if (pre.valid()) issue(1, pre);
+    uint4 ahead = make_uint4(0u, 0u, 0u, 0u); // thread 0: descriptor of the tile two ahead
+    if (tid == 0) {
+        if (ntile > 0) issue(0, a.tiles[t_begin]);
+        if (ntile > 1) issue(1, a.tiles[t_begin + 1]);
+        if (ntile > 2) ahead = a.tiles[t_begin + 2];
     }
 
-    for (u32 q = 0; cur.valid(); ++q) {
+    for (u32 q = 0; q < ntile; ++q) {
         const int st = q & 1;
-        const u32 s = cur.s;
-        const u32 tstart = cur.start;
-        const u32 tlen = cur.len;
-        const bool first_tile = cur.first_tile(a);
-        const bool last_tile = cur.last_tile();
-        const u32 j = a.shard_ss[s];
-        const u32 row_base = j * a.m;
+        // warp-uniform, so the warp-collective code below runs with every lane or none
+        const bool timed_out = __any_sync(0xffffffffu, !mbar_wait_bounded(&bar[st], (q >> 1) & 1u));
+        const uint4 d = sdesc[st];
+        const u32 tstart = d.x;
+        const u32 tlen = d.y & 0xffffu;
+        const u32 flags = d.y >> 16;
+        const u32 row_base = d.z * a.m;
         const u32 m_eff = min(a.m, a.I_out - row_base);
         const unsigned char *sb = smem_raw + (size_t)st * C::STAGE;
         const uint4 *selem = reinterpret_cast<const uint4 *>(sb);
         const u32 *snext = reinterpret_cast<const u32 *>(sb + (size_t)CAP * C::EB) + (tstart & 3u);
-
-        if (first_tile)
-            for (u32 i = tid; i < m_eff * (R / 4); i += C::THREADS)
-                reinterpret_cast<float4 *>(acc)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-
-        // warp-uniform, so the warp-collective sort below runs with every lane or none
-        const bool timed_out = __any_sync(0xffffffffu, !mbar_wait_bounded(&bar[st], (q >> 1) & 1u));
 
         // 1. remap burst
         if (remap && !timed_out) {
@@ -290,118 +270,106 @@ __global__ void __launch_bounds__(256, kBlocksPerSM) fused_mttkrp_remap_kernel(c
                 }
 #pragma unroll
                 for (int t = 0; t < C::EW; ++t) r[t] = (t < N) ? w[(t + 1) % N] : w[t];
-                const size_t d = snext[i];
+                const size_t dst = snext[i];
 #pragma unroll
                 for (int c = 0; c < C::EQ; ++c)
-                    eout[d * C::EQ + c] = make_uint4(r[4 * c], r[4 * c + 1], r[4 * c + 2], r[4 * c + 3]);
+                    eout[dst * C::EQ + c] = make_uint4(r[4 * c], r[4 * c + 1], r[4 * c + 2], r[4 * c + 3]);
             }
         }
 
-        // 2. compute this group's slice of the tile (stored sorted by row).  An odd
-        // slice length keeps the groups of a warp on different shared-memory banks.
-        u32 chunk = (tlen + G - 1) / G;
-        chunk |= 1u;
+        // 2. compute this group's slice [lo, hi) of the tile (stored sorted by
+        // row).  An odd slice length keeps the groups of a warp on different
+        // shared-memory banks.  Every group runs the same number of steps:
+        // positions past the slice end repeat the slice's last nonzero with
+        // weight 0 (same row, so no run ends there), and an empty slice
+        // repeats the tile's last nonzero the same way.
+        const u32 chunk = ((tlen + G - 1) / G) | 1u;
         const u32 geff = (tlen + chunk - 1) / chunk;
         const u32 lo = min((u32)grp * chunk, tlen);
-        const u32 hi = min((u32)(grp + 1) * chunk, tlen);
+        const u32 hi = min(lo + chunk, tlen);
+        const u32 last = (lo < hi) ? hi - 1 : tlen - 1;
         float racc[VEC];
 #pragma unroll
         for (int v = 0; v < VEC; ++v) racc[v] = 0.f;
-        u32 crow = kInvalidRow;
-        bool first = true;
-        if (!timed_out) {
-            // ping-pong batches: the gathers of batch b+1 are in flight while batch b is consumed
-            struct Batch {
-                uint4 raw[C::SUB][CPOPT ? N : N - 1];
-                u32 row[C::SUB];
-                float val[C::SUB];
-            };
-            auto load_batch = [&](u32 j0, Batch &B) {
+        u32 crow = min(selem[(size_t)min(lo, last) * C::EQ].x - row_base, (u32)M - 1u);
+        bool first_run = true;
+        auto steps = [&](u32 j0, auto count) {
+            constexpr int UU = decltype(count)::value;
+            u32 w[UU][N + 1];
+            uint4 y[UU][NF];
 #pragma unroll
-                for (int u = 0; u < C::SUB; ++u) {
-                    const u32 p = lo + j0 + u;
-                    const bool v = p < hi;
-                    // position 0 always exists (tlen >= 1): a stand-in for out-of-slice slots
-                    const u32 e = v ? p : 0u;
-                    u32 w[C::EW];
+            for (int u = 0; u < UU; ++u) {
+                const u32 p = min(lo + j0 + u, last);
 #pragma unroll
-                    for (int c = 0; c < C::EQ; ++c) {
-                        const uint4 x = selem[e * C::EQ + c];
-                        w[4 * c] = x.x;
-                        w[4 * c + 1] = x.y;
-                        w[4 * c + 2] = x.z;
-                        w[4 * c + 3] = x.w;
-                    }
-                    B.row[u] = v ? min(w[0] - row_base, (u32)M - 1u) : kInvalidRow;
-                    B.val[u] = __uint_as_float(w[N]);
+                for (int c = 0; c < C::EQ; ++c) {
+                    const uint4 x = selem[(size_t)p * C::EQ + c];
+                    const u32 xs[4] = {x.x, x.y, x.z, x.w};
 #pragma unroll
-                    for (int t = 1; t < N; ++t) B.raw[u][t - 1] = __ldg(Yp[t - 1] + (size_t)w[t] * RV);
-                    if constexpr (CPOPT) B.raw[u][N - 1] = __ldg(Yo + (size_t)w[0] * RV);
+                    for (int e = 0; e < 4; ++e)
+                        if (4 * c + e <= N) w[u][4 * c + e] = xs[e];
                 }
-            };
-            auto run_batch = [&](const Batch &B) {
-#pragma unroll
-                for (int u = 0; u < C::SUB; ++u) {
-                    float prod[VEC];
-                    widen<BF16>(B.raw[u][0], prod);
-#pragma unroll
-                    for (int t = 1; t < N - 1; ++t) {
-                        float f[VEC];
-                        widen<BF16>(B.raw[u][t], f);
-#pragma unroll
-                        for (int v = 0; v < VEC; ++v) prod[v] *= f[v];
-                    }
-                    float coef = B.val[u];
-                    if constexpr (CPOPT) {
-                        // model value m = <Y_n[c_n], prod>: lane partials summed over the group
-                        // (every lane runs the shuffles, so out-of-slice slots take part too)
-                        float yo[VEC];
-                        widen<false>(B.raw[u][N - 1], yo);
-                        float mpart = 0.f;
-#pragma unroll
-                        for (int v = 0; v < VEC; ++v) mpart = fmaf(yo[v], prod[v], mpart);
-#pragma unroll
-                        for (int off = C::L / 2; off >= 1; off >>= 1) mpart += __shfl_xor_sync(0xffffffffu, mpart, off);
-                        const float e = B.val[u] - mpart;  // residual x - m
-                        if (B.row[u] != kInvalidRow && k == 0) loss += (double)e * (double)e;
-                        coef = -e;                          // dL/dY_n += -e * prod
-                    }
-                    if (B.row[u] == kInvalidRow) continue;
-                    if (B.row[u] != crow) {
-                        if (crow != kInvalidRow) {
-                            if (first) {
-                                store_vec<VEC>(my_hacc, racc);
-                                if (k == 0) hrow[grp] = crow;
-                                first = false;
-                            } else {
-                                // a row that starts and ends inside this slice: only this group holds it
-                                float *dst = acc + crow * R + k * VEC;
-                                add_vec<VEC>(racc, dst);
-                                store_vec<VEC>(dst, racc);
-                            }
-                        }
-                        crow = B.row[u];
-#pragma unroll
-                        for (int v = 0; v < VEC; ++v) racc[v] = 0.f;
-                    }
-#pragma unroll
-                    for (int v = 0; v < VEC; ++v) racc[v] = fmaf(coef, prod[v], racc[v]);
-                }
-            };
-            Batch A, Bb;
-            load_batch(0u, A);
-            for (u32 j0 = 0; j0 < chunk; j0 += 2 * C::SUB) {
-                const bool more1 = j0 + C::SUB < chunk;
-                if (more1) load_batch(j0 + C::SUB, Bb);
-                run_batch(A);
-                if (!more1) break;
-                if (j0 + 2 * C::SUB < chunk) load_batch(j0 + 2 * C::SUB, A);
-                run_batch(Bb);
             }
+#pragma unroll
+            for (int u = 0; u < UU; ++u) {
+#pragma unroll
+                for (int t = 0; t < N - 1; ++t) y[u][t] = __ldg(Yp[t] + (size_t)w[u][t + 1] * RV);
+                if constexpr (CPOPT) y[u][N - 1] = __ldg(Yo + (size_t)w[u][0] * RV);
+            }
+#pragma unroll
+            for (int u = 0; u < UU; ++u) {
+                const bool valid = lo + j0 + u < hi;
+                const u32 row = min(w[u][0] - row_base, (u32)M - 1u);
+                float prod[VEC];
+                widen<BF16>(y[u][0], prod);
+#pragma unroll
+                for (int t = 1; t < N - 1; ++t) {
+                    float f[VEC];
+                    widen<BF16>(y[u][t], f);
+#pragma unroll
+                    for (int v = 0; v < VEC; ++v) prod[v] *= f[v];
+                }
+                const float val = __uint_as_float(w[u][N]);
+                float coef = valid ? val : 0.f;
+                if constexpr (CPOPT) {
+                    // model value m = <Y_n[c_n], prod>: lane partials summed over the group
+                    float yo[VEC];
+                    widen<false>(y[u][N - 1], yo);
+                    float mpart = 0.f;
+#pragma unroll
+                    for (int v = 0; v < VEC; ++v) mpart = fmaf(yo[v], prod[v], mpart);
+#pragma unroll
+                    for (int off = C::L / 2; off >= 1; off >>= 1) mpart += __shfl_xor_sync(0xffffffffu, mpart, off);
+                    const float e = val - mpart; // residual x - m
+                    if (valid && k == 0) loss += (double)e * (double)e;
+                    coef = valid ? -e : 0.f;     // dL/dY_n += -e * prod
+                }
+                if (row != crow) {
+                    if (first_run) {
+                        store_vec<VEC>(my_hacc, racc);
+                        if (k == 0) hrow[grp] = crow;
+                        first_run = false;
+                    } else {
+                        // a row that starts and ends inside this slice: only this group holds it
+                        float *dst = acc + crow * R + k * VEC;
+                        add_vec<VEC>(racc, dst);
+                        store_vec<VEC>(dst, racc);
+                    }
+                    crow = row;
+#pragma unroll
+                    for (int v = 0; v < VEC; ++v) racc[v] = 0.f;
+                }
+#pragma unroll
+                for (int v = 0; v < VEC; ++v) racc[v] = fmaf(coef, prod[v], racc[v]);
+            }
+        };
+        if (!timed_out) {
+            u32 j0 = 0;
+            for (; j0 + U <= chunk; j0 += U) steps(j0, std::integral_constant<int, U>{});
+            for (; j0 < chunk; ++j0) steps(j0, std::integral_constant<int, 1>{});
         }
         // slice summary: a single run in the head slot, else the last run in the tail slot
         if ((u32)grp < geff) {
-            if (first) {
+            if (first_run) {
                 store_vec<VEC>(my_hacc, racc);
                 if (k == 0) {
                     hrow[grp] = crow;
@@ -416,13 +384,18 @@ __global__ void __launch_bounds__(256, kBlocksPerSM) fused_mttkrp_remap_kernel(c
             }
         }
         if (__syncthreads_or(timed_out)) {
-            if (tid == 0) atomicOr(a.err, 1u);
+            if (tid == 0) {
+                atomicOr(a.err, 1u);
+                // let the copies still in flight land before the block's shared memory is released
+                mbar_wait_bounded(&bar[st], (q >> 1) & 1u);
+                if (q + 1 < ntile) mbar_wait_bounded(&bar[st ^ 1], ((q + 1) >> 1) & 1u);
+            }
             return;
         }
         // every thread is past its reads of this stage: load the tile after next into it
-        if (tid == 0) {
-            pre.advance(a);
-            if (pre.valid()) issue(st, pre);
+        if (tid == 0 && q + 2 < ntile) {
+            issue(st, ahead);
+            if (q + 3 < ntile) ahead = a.tiles[t_begin + q + 3];
         }
 
         // 3. runs that touch a slice boundary: summed in slice order by the group
@@ -459,15 +432,19 @@ __global__ void __launch_bounds__(256, kBlocksPerSM) fused_mttkrp_remap_kernel(c
 
         // the next tile's slices may hold any of these rows: their adds wait here
         __syncthreads();
-        // end of the shard: its super-shard's rows to the output, or to the shard's row block
-        if (last_tile) {
-            const bool alone = a.ss_shard_ptr[j + 1] - a.ss_shard_ptr[j] == 1u;
-            float4 *dst = alone ? reinterpret_cast<float4 *>(a.out + (size_t)row_base * R)
-                                : reinterpret_cast<float4 *>(a.partials + (size_t)s * a.m * R);
-            for (u32 i = tid; i < m_eff * (R / 4); i += C::THREADS) dst[i] = reinterpret_cast<const float4 *>(acc)[i];
+        // end of the shard: its super-shard's rows to the output (the only shard of
+        // its super-shard) or to the shard's row block, and the accumulator back to zero
+        if (flags & kTileLast) {
+            float4 *dst = (flags & kTileAlone) ? reinterpret_cast<float4 *>(a.out + (size_t)row_base * R)
+                                               : reinterpret_cast<float4 *>(a.partials + (size_t)d.w * a.m * R);
+            const u32 nout = m_eff * (R / 4);
+            for (u32 i = tid; i < (u32)(M * R / 4); i += C::THREADS) {
+                float4 *ai = reinterpret_cast<float4 *>(acc) + i;
+                if (i < nout) dst[i] = *ai;
+                *ai = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
             __syncthreads();
         }
-        cur.advance(a);
     }
     if constexpr (CPOPT) {
         // half the sum of squared residuals of this block, reduced in a fixed order

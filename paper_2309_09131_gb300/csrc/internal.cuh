@@ -78,7 +78,12 @@ struct ModeMeta {
     std::vector<u32> sh_bin_ptr, sh_items;  // Algorithm 3 over shards (kernel schedule)
     std::vector<u32> k4_items;              // super-shards whose rows K4 writes (not exactly one shard)
     std::vector<u32> tile_ptr;              // T + 1: layout tiles (K1 only)
-    DevBuf d_shard_ptr, d_shard_ss, d_ss_shard_ptr, d_bin_ptr, d_items, d_k4, d_next;
+    // tile descriptors in block-schedule order (bin b: tiles [tile_bin_ptr[b],
+    // tile_bin_ptr[b+1])), four words each: start, len | flags << 16,
+    // super-shard, shard; flags: 1 first tile of its shard, 2 last tile,
+    // 4 the super-shard has no other shard
+    std::vector<u32> tiles, tile_bin_ptr;
+    DevBuf d_shard_ptr, d_shard_ss, d_ss_shard_ptr, d_bin_ptr, d_items, d_k4, d_next, d_tiles, d_tile_bin_ptr;
 };
 
 // CP-ALS workspace (als.cu), allocated by the first flycoo_cp_als_step
@@ -146,9 +151,10 @@ constexpr u32 kSpinLimit = 1u << 24;
 #define FLYCOO_BLOCKS_PER_SM 3
 #endif
 constexpr int kBlocksPerSM = FLYCOO_BLOCKS_PER_SM;
-// nonzeros of a 3-mode tensor whose factor-row gathers are issued together
-#ifndef FLYCOO_SUB3
-#define FLYCOO_SUB3 2
+// nonzeros of a 3-mode tensor whose factor-row gathers one thread group issues
+// together (each step of the fused kernel's inner loop)
+#ifndef FLYCOO_UNROLL3
+#define FLYCOO_UNROLL3 4
 #endif
 
 inline int elem_words_for(int N) { return (N + 1 <= 4) ? 4 : 8; }
@@ -185,6 +191,8 @@ struct FusedArgs {
     const u32 *shard_ss;       // S
     const u32 *ss_shard_ptr;   // k + 1
     const u32 *bin_ptr, *bin_items;
+    const uint4 *tiles;        // tile descriptors, block-schedule order
+    const u32 *tile_bin_ptr;   // bins + 1
     float *partials;           // row block of shard s at s * m * R
     u32 *err;                  // device error word
     const void *Yout;          // CP-OPT pass: the output mode's factor (nullptr: plain spMTTKRP)
