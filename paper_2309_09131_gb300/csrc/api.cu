@@ -31,7 +31,8 @@ u64 Tensor::device_bytes() const {
     for (int n = 0; n < N; ++n) {
         const ModeMeta &m = mode[n];
         b += m.d_shard_ptr.bytes + m.d_shard_ss.bytes + m.d_ss_shard_ptr.bytes + m.d_bin_ptr.bytes +
-             m.d_items.bytes + m.d_k4.bytes + m.d_next.bytes + m.d_tiles.bytes + m.d_tile_bin_ptr.bytes;
+             m.d_items.bytes + m.d_k4.bytes + m.d_next.bytes + m.d_tiles[0].bytes + m.d_tiles[1].bytes +
+             m.d_tile_bin_ptr[0].bytes + m.d_tile_bin_ptr[1].bytes;
     }
     return b;
 }
@@ -113,29 +114,33 @@ flycoo_status partition_mode(Tensor &t, int n, const std::vector<u32> &ssp, cuda
     md.tile_ptr.clear();
     for (u64 q = 0; q < md.S; ++q) {
         shard_size[q] = md.shard_ptr[q + 1] - md.shard_ptr[q];
-        for (u64 p = md.shard_ptr[q]; p < md.shard_ptr[q + 1]; p += kLayoutTile) md.tile_ptr.push_back((u32)p);
+        for (u64 p = md.shard_ptr[q]; p < md.shard_ptr[q + 1]; p += kSortTile) md.tile_ptr.push_back((u32)p);
     }
     md.tile_ptr.push_back((u32)t.nnz);
     lpt_schedule(ss_shards, t.bins, md.ss_bin_ptr, md.ss_items);
     lpt_schedule(shard_size, t.bins, md.sh_bin_ptr, md.sh_items);
-    // tile descriptors of the block schedule
-    md.tiles.clear();
-    md.tile_bin_ptr.assign((size_t)t.bins + 1, 0);
-    for (u32 b = 0; b < t.bins; ++b) {
-        md.tile_bin_ptr[b] = (u32)(md.tiles.size() / 4);
-        for (u64 it = md.sh_bin_ptr[b]; it < md.sh_bin_ptr[b + 1]; ++it) {
-            const u32 sh = md.sh_items[it];
-            const u32 j = md.shard_ss[sh];
-            const u32 lo = md.shard_ptr[sh], hi = md.shard_ptr[sh + 1];
-            const u32 alone = ss_shards[j] == 1 ? 4u : 0u;
-            for (u32 p = lo; p < hi; p += kLayoutTile) {
-                const u32 len = std::min<u32>(kLayoutTile, hi - p);
-                const u32 flags = (p == lo ? 1u : 0u) | (p + len == hi ? 2u : 0u) | alone;
-                md.tiles.insert(md.tiles.end(), {p, len | (flags << 16), j, sh});
+    // tile descriptors of the block schedule, for both stage-tile sizes
+    for (int z = 0; z < 2; ++z) {
+        const u32 tile = kStageTile[z];
+        std::vector<u32> &td = md.tiles[z];
+        td.clear();
+        md.tile_bin_ptr[z].assign((size_t)t.bins + 1, 0);
+        for (u32 b = 0; b < t.bins; ++b) {
+            md.tile_bin_ptr[z][b] = (u32)(td.size() / 4);
+            for (u64 it = md.sh_bin_ptr[b]; it < md.sh_bin_ptr[b + 1]; ++it) {
+                const u32 sh = md.sh_items[it];
+                const u32 j = md.shard_ss[sh];
+                const u32 lo = md.shard_ptr[sh], hi = md.shard_ptr[sh + 1];
+                const u32 alone = ss_shards[j] == 1 ? 4u : 0u;
+                for (u32 p = lo; p < hi; p += tile) {
+                    const u32 len = std::min<u32>(tile, hi - p);
+                    const u32 flags = (p == lo ? 1u : 0u) | (p + len == hi ? 2u : 0u) | alone;
+                    td.insert(td.end(), {p, len | (flags << 16), j, sh});
+                }
             }
         }
+        md.tile_bin_ptr[z][t.bins] = (u32)(td.size() / 4);
     }
-    md.tile_bin_ptr[t.bins] = (u32)(md.tiles.size() / 4);
     // K4 writes the rows of every super-shard that does not have exactly one shard
     md.k4_items.clear();
     for (u64 j = 0; j < md.k; ++j)
@@ -146,8 +151,10 @@ flycoo_status partition_mode(Tensor &t, int n, const std::vector<u32> &ssp, cuda
     FLY_TRY(upload(md.d_bin_ptr, md.sh_bin_ptr, s));
     FLY_TRY(upload(md.d_items, md.sh_items, s));
     FLY_TRY(upload(md.d_k4, md.k4_items, s));
-    FLY_TRY(upload(md.d_tiles, md.tiles, s));
-    FLY_TRY(upload(md.d_tile_bin_ptr, md.tile_bin_ptr, s));
+    for (int z = 0; z < 2; ++z) {
+        FLY_TRY(upload(md.d_tiles[z], md.tiles[z], s));
+        FLY_TRY(upload(md.d_tile_bin_ptr[z], md.tile_bin_ptr[z], s));
+    }
     return FLYCOO_OK;
 }
 
@@ -341,8 +348,10 @@ extern "C" flycoo_status flycoo_spmttkrp(flycoo_handle h, int mode, const void *
     a.ss_shard_ptr = md.d_ss_shard_ptr.as<u32>();
     a.bin_ptr = md.d_bin_ptr.as<u32>();
     a.bin_items = md.d_items.as<u32>();
-    a.tiles = md.d_tiles.as<uint4>();
-    a.tile_bin_ptr = md.d_tile_bin_ptr.as<u32>();
+    for (int z = 0; z < 2; ++z) {
+        a.tiles[z] = md.d_tiles[z].as<uint4>();
+        a.tile_bin_ptr[z] = md.d_tile_bin_ptr[z].as<u32>();
+    }
     a.partials = t.partials.as<float>();
     a.err = t.err.as<u32>();
     a.I_out = (u32)t.dims[mode];
@@ -416,8 +425,10 @@ flycoo_status flycoo::run_pass(Tensor &t, int mode, const void *const *F, flycoo
     a.ss_shard_ptr = md.d_ss_shard_ptr.as<u32>();
     a.bin_ptr = md.d_bin_ptr.as<u32>();
     a.bin_items = md.d_items.as<u32>();
-    a.tiles = md.d_tiles.as<uint4>();
-    a.tile_bin_ptr = md.d_tile_bin_ptr.as<u32>();
+    for (int z = 0; z < 2; ++z) {
+        a.tiles[z] = md.d_tiles[z].as<uint4>();
+        a.tile_bin_ptr[z] = md.d_tile_bin_ptr[z].as<u32>();
+    }
     a.partials = t.partials.as<float>();
     a.err = t.err.as<u32>();
     a.Yout = Yout;
@@ -595,7 +606,7 @@ extern "C" flycoo_status flycoo_get_info(flycoo_handle h, flycoo_info *out) {
     out->g = t.g;
     out->bins = t.bins;
     out->elem_bytes = (uint32_t)(t.elem_words * 4);
-    out->tile = kLayoutTile;
+    out->tile = kSortTile;
     for (int n = 0; n < t.N; ++n) {
         out->dims[n] = t.dims[n];
         out->m[n] = t.mode[n].m;

@@ -58,12 +58,18 @@ struct FusedCfg {
     static constexpr int EQ = EW / 4;               // 16-byte chunks per stored nonzero
     static constexpr int EB = EW * 4;               // bytes per stored nonzero
     static constexpr int M = (int)kMaxSuperShardRows;
-    static constexpr int CAP = (int)kLayoutTile;    // one layout tile per stage
-    // shared memory
-    static constexpr size_t STAGE = (size_t)CAP * EB + ((size_t)CAP + 8) * 4; // nonzeros + their next slots
-    static constexpr size_t ACC = (size_t)M * R * 4;                           // row accumulators
-    static constexpr size_t SUMBUF = 2 * (size_t)G * R * 4 + 3 * (size_t)G * 4; // slice summaries
-    static constexpr size_t SMEM = 2 * STAGE + ACC + SUMBUF + 64;
+    // shared memory: two stages (nonzeros + their next slots), the row
+    // accumulators and the slice summaries
+    static constexpr size_t stage_bytes(size_t cap) { return cap * EB + (cap + 8) * 4; }
+    static constexpr size_t ACC = (size_t)M * R * 4;
+    static constexpr size_t SUMBUF = 2 * (size_t)G * R * 4 + 3 * (size_t)G * 4;
+    static constexpr size_t smem_bytes(size_t cap) { return 2 * stage_bytes(cap) + ACC + SUMBUF + 64; }
+    // the larger stage tile when kBlocksPerSM blocks of it fit in an SM's 228 KB
+    // (1 KB of each block is reserved by the system)
+    static constexpr int TZ = (kBlocksPerSM * (smem_bytes(kStageTile[1]) + 1024) <= 228 * 1024) ? 1 : 0;
+    static constexpr int CAP = (int)kStageTile[TZ];
+    static constexpr size_t STAGE = stage_bytes(CAP);
+    static constexpr size_t SMEM = smem_bytes(CAP);
     static_assert(R % VEC == 0 && L >= 1 && L <= 32 && 32 % L == 0, "rank not supported");
     static_assert(STAGE % 16 == 0 && SUMBUF % 16 == 0 && ACC % 16 == 0, "shared-memory alignment");
 };
@@ -206,8 +212,9 @@ __global__ void __launch_bounds__(256, kBlocksPerSM) fused_mttkrp_remap_kernel(c
     double loss = 0.0;
     float *my_hacc = hacc + grp * R + k * VEC;
     float *my_tacc = tacc + grp * R + k * VEC;
-    const u32 t_begin = a.tile_bin_ptr[blockIdx.x];
-    const u32 ntile = a.tile_bin_ptr[blockIdx.x + 1] - t_begin;
+    const uint4 *__restrict__ tiles = a.tiles[C::TZ];
+    const u32 t_begin = a.tile_bin_ptr[C::TZ][blockIdx.x];
+    const u32 ntile = a.tile_bin_ptr[C::TZ][blockIdx.x + 1] - t_begin;
 
     // the accumulator starts at zero; the flush at the end of every shard zeroes it again
     for (u32 i = tid; i < (u32)(M * R / 4); i += C::THREADS)
@@ -237,9 +244,9 @@ __global__ void __launch_bounds__(256, kBlocksPerSM) fused_mttkrp_remap_kernel(c
     };
     uint4 ahead = make_uint4(0u, 0u, 0u, 0u); // thread 0: descriptor of the tile two ahead
     if (tid == 0) {
-        if (ntile > 0) issue(0, a.tiles[t_begin]);
-        if (ntile > 1) issue(1, a.tiles[t_begin + 1]);
-        if (ntile > 2) ahead = a.tiles[t_begin + 2];
+        if (ntile > 0) issue(0, tiles[t_begin]);
+        if (ntile > 1) issue(1, tiles[t_begin + 1]);
+        if (ntile > 2) ahead = tiles[t_begin + 2];
     }
 
     for (u32 q = 0; q < ntile; ++q) {
@@ -395,7 +402,7 @@ __global__ void __launch_bounds__(256, kBlocksPerSM) fused_mttkrp_remap_kernel(c
         // every thread is past its reads of this stage: load the tile after next into it
         if (tid == 0 && q + 2 < ntile) {
             issue(st, ahead);
-            if (q + 3 < ntile) ahead = a.tiles[t_begin + q + 3];
+            if (q + 3 < ntile) ahead = tiles[t_begin + q + 3];
         }
 
         // 3. runs that touch a slice boundary: summed in slice order by the group

@@ -82,8 +82,10 @@ struct ModeMeta {
     // tile_bin_ptr[b+1])), four words each: start, len | flags << 16,
     // super-shard, shard; flags: 1 first tile of its shard, 2 last tile,
     // 4 the super-shard has no other shard
-    std::vector<u32> tiles, tile_bin_ptr;
-    DevBuf d_shard_ptr, d_shard_ss, d_ss_shard_ptr, d_bin_ptr, d_items, d_k4, d_next, d_tiles, d_tile_bin_ptr;
+    // (one set per stage-tile size, kStageTile)
+    std::vector<u32> tiles[2], tile_bin_ptr[2];
+    DevBuf d_shard_ptr, d_shard_ss, d_ss_shard_ptr, d_bin_ptr, d_items, d_k4, d_next;
+    DevBuf d_tiles[2], d_tile_bin_ptr[2];
 };
 
 // CP-ALS workspace (als.cu), allocated by the first flycoo_cp_als_step
@@ -136,10 +138,18 @@ constexpr int kMaxRank = 64;
 // largest super-shard width m_n: the fused kernel keeps a super-shard's output
 // rows (m_n x R FP32) in shared memory
 constexpr u32 kMaxSuperShardRows = 128;
-// layout tile: inside a shard, each run of kLayoutTile positions (counted from
-// the shard start) is stored sorted by output index; the fused kernel works
-// tile by tile
-constexpr u32 kLayoutTile = 512;
+// sort unit: inside a shard, each run of kSortTile positions (counted from the
+// shard start) is stored sorted by output index (K1), so a row's nonzeros are
+// contiguous within it
+#ifndef FLYCOO_SORT_TILE
+#define FLYCOO_SORT_TILE 2048
+#endif
+constexpr u32 kSortTile = FLYCOO_SORT_TILE;
+// stage tiles: the fused kernel streams a shard one stage tile at a time, 1024
+// positions when three blocks of that size fit on an SM, else 512; both nest
+// inside sort units, and the schedule is described for both sizes
+constexpr u32 kStageTile[2] = {512u, 1024u};
+static_assert(kSortTile % 1024u == 0, "a sort unit is a whole number of stage tiles");
 constexpr u32 kInvalidRow = 0xffffffffu;
 // iteration limit of every device-side wait (mbarrier polls); ~0.1-1 s
 constexpr u32 kSpinLimit = 1u << 24;
@@ -191,8 +201,8 @@ struct FusedArgs {
     const u32 *shard_ss;       // S
     const u32 *ss_shard_ptr;   // k + 1
     const u32 *bin_ptr, *bin_items;
-    const uint4 *tiles;        // tile descriptors, block-schedule order
-    const u32 *tile_bin_ptr;   // bins + 1
+    const uint4 *tiles[2];     // tile descriptors, block-schedule order, per stage-tile size
+    const u32 *tile_bin_ptr[2]; // bins + 1, per stage-tile size
     float *partials;           // row block of shard s at s * m * R
     u32 *err;                  // device error word
     const void *Yout;          // CP-OPT pass: the output mode's factor (nullptr: plain spMTTKRP)

@@ -7,7 +7,7 @@
 // L_0 is the input order stably sorted by ss_1, ss_2, ..., ss_{N-1} and
 // finally ss_0.  K1 therefore runs 2N-1 stable sorts, each a few 8-bit LSD
 // radix passes (histogram, exclusive scan, stable scatter).  The stored order
-// then sorts every layout tile (kLayoutTile positions of a shard) by output
+// then sorts every sort unit (kSortTile positions of a shard) by output
 // index, stably, so the fused kernel finds each row of a tile contiguous.  Every
 // step is integer work with no atomics on the data path, so the layouts,
 // pointers and remap permutations are bit-exact and deterministic.  There is
@@ -315,7 +315,7 @@ __global__ void export_layout_kernel(const u32 *elem, int ew, int N, int layout,
     }
 }
 
-// Layout tiles: inside every shard, runs of kLayoutTile positions (from the
+// Sort units: inside every shard, runs of kSortTile positions (from the
 // shard start) are stored sorted by output index (stable).  One block per
 // tile: per-warp row counts, a scan, then stable ranks from __match_any_sync.
 __global__ void __launch_bounds__(256)

@@ -134,8 +134,10 @@ extern "C" flycoo_status flycoo_spmttkrp_static_scratch(flycoo_handle h, int mod
     a.ss_shard_ptr = md.d_ss_shard_ptr.as<u32>();
     a.bin_ptr = md.d_bin_ptr.as<u32>();
     a.bin_items = md.d_items.as<u32>();
-    a.tiles = md.d_tiles.as<uint4>();
-    a.tile_bin_ptr = md.d_tile_bin_ptr.as<u32>();
+    for (int z = 0; z < 2; ++z) {
+        a.tiles[z] = md.d_tiles[z].as<uint4>();
+        a.tile_bin_ptr[z] = md.d_tile_bin_ptr[z].as<u32>();
+    }
     a.partials = scratch;
     a.err = t.err.as<u32>();
     a.I_out = (u32)t.dims[mode];

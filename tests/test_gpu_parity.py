@@ -55,7 +55,7 @@ def test_layout_partition_schedule_bitexact(P, case):
     info = T.info
     N = len(dims)
     assert info["nnz"] == nnz and info["layout_mode"] == 0
-    ref = oracle.flycoo_layout(idx, dims, info["m"], info["g"], info["bins"])
+    ref = oracle.flycoo_layout(idx, dims, info["m"], info["g"], info["bins"], tile=info["tile"])
     for n in range(N):
         ss, sp, sss = T.export_partition(n)
         np.testing.assert_array_equal(ss, ref[n]["ss_ptr"])
