@@ -62,7 +62,7 @@ struct FusedCfg {
     // accumulators and the slice summaries
     static constexpr size_t stage_bytes(size_t cap) { return cap * EB + (cap + 8) * 4; }
     static constexpr size_t ACC = (size_t)M * R * 4;
-    static constexpr size_t SUMBUF = 2 * (size_t)G * R * 4 + 3 * (size_t)G * 4;
+    static constexpr size_t SUMBUF = (size_t)G * R * 4 + (((size_t)G * 4 + 15) & ~(size_t)15);
     static constexpr size_t smem_bytes(size_t cap) { return 2 * stage_bytes(cap) + ACC + SUMBUF + 64; }
     // the larger stage tile when kBlocksPerSM blocks of it fit in an SM's 228 KB
     // (1 KB of each block is reserved by the system)
@@ -185,16 +185,15 @@ __global__ void __launch_bounds__(256, kBlocksPerSM) fused_mttkrp_remap_kernel(c
     constexpr int G = C::G;
     constexpr int M = C::M;
     constexpr int NF = CPOPT ? N : N - 1;            // factor rows gathered per nonzero
-    constexpr int U = (N == 3 && !CPOPT) ? (BF16 ? FLYCOO_UNROLL3 - 1 : FLYCOO_UNROLL3) : 2; // nonzeros per group per step
+    constexpr int U = (N == 3 && !CPOPT) ? FLYCOO_UNROLL3 : (N >= 5 ? 1 : 2); // nonzeros per group per step
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float *acc = reinterpret_cast<float *>(smem_raw + 2 * C::STAGE);          // [M][R]
-    float *hacc = acc + M * R;                                               // [G][R]
-    float *tacc = hacc + G * R;                                              // [G][R]
-    u32 *hrow = reinterpret_cast<u32 *>(tacc + G * R);                       // [G]
-    u32 *trow = hrow + G;
-    u32 *multi = trow + G;
+    float *hacc = acc + M * R;                                               // [G][R] head partials
+    u32 *pass = reinterpret_cast<u32 *>(hacc + G * R);                       // [G]
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw + 2 * C::STAGE + C::ACC + C::SUMBUF);
-    uint4 *sdesc = reinterpret_cast<uint4 *>(bar + 2); // descriptor of the tile in each stage
+    // sdesc[0..1]: descriptor of the tile in each stage; sdesc[2]: thread 0's
+    // copy of the descriptor of the tile two ahead
+    uint4 *sdesc = reinterpret_cast<uint4 *>(bar + 2);
 
     const int tid = threadIdx.x;
     const int lane = tid & 31;
@@ -211,7 +210,6 @@ __global__ void __launch_bounds__(256, kBlocksPerSM) fused_mttkrp_remap_kernel(c
     const uint4 *Yo = CPOPT ? static_cast<const uint4 *>(a.Yout) + k : nullptr;
     double loss = 0.0;
     float *my_hacc = hacc + grp * R + k * VEC;
-    float *my_tacc = tacc + grp * R + k * VEC;
     const uint4 *__restrict__ tiles = a.tiles[C::TZ];
     const u32 t_begin = a.tile_bin_ptr[C::TZ][blockIdx.x];
     const u32 ntile = a.tile_bin_ptr[C::TZ][blockIdx.x + 1] - t_begin;
@@ -242,11 +240,10 @@ __global__ void __launch_bounds__(256, kBlocksPerSM) fused_mttkrp_remap_kernel(c
         tma_load_1d(sb, ein + (size_t)start * C::EQ, len * C::EB, &bar[st]);
         if (remap) tma_load_1d(sb + (size_t)CAP * C::EB, a.next + nlo, (nhi - nlo) * 4u, &bar[st]);
     };
-    uint4 ahead = make_uint4(0u, 0u, 0u, 0u); // thread 0: descriptor of the tile two ahead
     if (tid == 0) {
         if (ntile > 0) issue(0, tiles[t_begin]);
         if (ntile > 1) issue(1, tiles[t_begin + 1]);
-        if (ntile > 2) ahead = tiles[t_begin + 2];
+        if (ntile > 2) sdesc[2] = tiles[t_begin + 2];
     }
 
     for (u32 q = 0; q < ntile; ++q) {
@@ -284,22 +281,32 @@ __global__ void __launch_bounds__(256, kBlocksPerSM) fused_mttkrp_remap_kernel(c
             }
         }
 
-        // 2. compute this group's slice [lo, hi) of the tile (stored sorted by
-        // row).  An odd slice length keeps the groups of a warp on different
-        // shared-memory banks.  Every group runs the same number of steps:
-        // positions past the slice end repeat the slice's last nonzero with
-        // weight 0 (same row, so no run ends there), and an empty slice
-        // repeats the tile's last nonzero the same way.
+        // 2. compute this group's slice [lo, hi) of the tile, which is stored
+        // sorted by row inside each sort unit.  Slices are chunk positions long
+        // (odd, so the groups of a warp read different shared-memory banks).  A
+        // run of one row that lies inside the slice is added by this group
+        // alone; a run that crosses a slice edge is summed in step 3.
         const u32 chunk = ((tlen + G - 1) / G) | 1u;
         const u32 geff = (tlen + chunk - 1) / chunk;
+        const u32 *sw = reinterpret_cast<const u32 *>(sb); // word 0 of a stored nonzero is its row index
         const u32 lo = min((u32)grp * chunk, tlen);
         const u32 hi = min(lo + chunk, tlen);
+        // the slice's first run continues the previous slice's row / its last run
+        // continues into the next slice
+        const bool head_shared = lo > 0 && lo < hi && sw[(size_t)lo * C::EW] == sw[(size_t)(lo - 1) * C::EW];
+        const bool tail_shared = hi < tlen && lo < hi && sw[(size_t)hi * C::EW] == sw[(size_t)(hi - 1) * C::EW];
+        // every group of a warp runs the same number of steps: positions past
+        // the slice end repeat the slice's last nonzero with weight 0 (same
+        // row, so no run ends there), and an empty slice repeats the tile's
+        // last nonzero the same way
+        const u32 wlen = chunk;
         const u32 last = (lo < hi) ? hi - 1 : tlen - 1;
         float racc[VEC];
 #pragma unroll
         for (int v = 0; v < VEC; ++v) racc[v] = 0.f;
-        u32 crow = min(selem[(size_t)min(lo, last) * C::EQ].x - row_base, (u32)M - 1u);
-        bool first_run = true;
+        u32 crow = min(sw[(size_t)min(lo, last) * C::EW] - row_base, (u32)M - 1u);
+        // the first run goes to the head slot when it continues the previous slice's row
+        bool first_run = head_shared;
         auto steps = [&](u32 j0, auto count) {
             constexpr int UU = decltype(count)::value;
             u32 w[UU][N + 1];
@@ -353,10 +360,10 @@ __global__ void __launch_bounds__(256, kBlocksPerSM) fused_mttkrp_remap_kernel(c
                 if (row != crow) {
                     if (first_run) {
                         store_vec<VEC>(my_hacc, racc);
-                        if (k == 0) hrow[grp] = crow;
+                        if (k == 0) pass[grp] = 0u;
                         first_run = false;
                     } else {
-                        // a row that starts and ends inside this slice: only this group holds it
+                        // a whole row of this tile: only this group holds it
                         float *dst = acc + crow * R + k * VEC;
                         add_vec<VEC>(racc, dst);
                         store_vec<VEC>(dst, racc);
@@ -371,26 +378,32 @@ __global__ void __launch_bounds__(256, kBlocksPerSM) fused_mttkrp_remap_kernel(c
         };
         if (!timed_out) {
             u32 j0 = 0;
-            for (; j0 + U <= chunk; j0 += U) steps(j0, std::integral_constant<int, U>{});
-            for (; j0 < chunk; ++j0) steps(j0, std::integral_constant<int, 1>{});
+            for (; j0 + U <= wlen; j0 += U) steps(j0, std::integral_constant<int, U>{});
+            for (; j0 < wlen; ++j0) steps(j0, std::integral_constant<int, 1>{});
         }
-        // slice summary: a single run in the head slot, else the last run in the tail slot
-        if ((u32)grp < geff) {
-            if (first_run) {
+        // the slice's last run: added here when it ends at the slice end, else kept
+        // for step 3 (in registers when its row starts in this slice, in the head
+        // slot, marked pass-through, when the whole slice is one piece of a longer row)
+        bool chain_start = false;
+        if (!timed_out && lo < hi) {
+            if (tail_shared) {
+                if (first_run) {
+                    store_vec<VEC>(my_hacc, racc);
+                    if (k == 0) pass[grp] = 1u;
+                } else {
+                    chain_start = true;
+                }
+            } else if (first_run) {
                 store_vec<VEC>(my_hacc, racc);
-                if (k == 0) {
-                    hrow[grp] = crow;
-                    multi[grp] = 0u;
-                }
+                if (k == 0) pass[grp] = 0u;
             } else {
-                store_vec<VEC>(my_tacc, racc);
-                if (k == 0) {
-                    trow[grp] = crow;
-                    multi[grp] = 1u;
-                }
+                float *dst = acc + crow * R + k * VEC;
+                add_vec<VEC>(racc, dst);
+                store_vec<VEC>(dst, racc);
             }
         }
-        if (__syncthreads_or(timed_out)) {
+        const int nsync = __syncthreads_count(timed_out ? 1024 : (chain_start && k == 0 ? 1 : 0));
+        if (nsync >= 1024) {
             if (tid == 0) {
                 atomicOr(a.err, 1u);
                 // let the copies still in flight land before the block's shared memory is released
@@ -401,44 +414,26 @@ __global__ void __launch_bounds__(256, kBlocksPerSM) fused_mttkrp_remap_kernel(c
         }
         // every thread is past its reads of this stage: load the tile after next into it
         if (tid == 0 && q + 2 < ntile) {
-            issue(st, ahead);
-            if (q + 3 < ntile) ahead = tiles[t_begin + q + 3];
+            issue(st, sdesc[2]);
+            if (q + 3 < ntile) sdesc[2] = tiles[t_begin + q + 3];
         }
 
-        // 3. runs that touch a slice boundary: summed in slice order by the group
-        // where they start, then added to the accumulator
-        if ((u32)grp < geff) {
-            auto extend = [&](u32 r, float *sum) {
+        // 3. rows longer than a chunk: the group where such a row starts adds the
+        // head partials of the following slices, in slice order, through the last
+        // one that is not a pass-through, then adds the sum to the accumulator
+        if (nsync > 0) {
+            if (chain_start) {
                 for (u32 g2 = grp + 1; g2 < geff; ++g2) {
-                    if (hrow[g2] != r) return;
-                    add_vec<VEC>(sum, hacc + g2 * R + k * VEC);
-                    if (multi[g2]) return;
+                    add_vec<VEC>(racc, hacc + g2 * R + k * VEC);
+                    if (!pass[g2]) break;
                 }
-            };
-            const u32 h = hrow[grp];
-            const bool mg = multi[grp] != 0u;
-            const u32 prev_last = (grp == 0) ? kInvalidRow : (multi[grp - 1] ? trow[grp - 1] : hrow[grp - 1]);
-            if (grp == 0 || prev_last != h) {
-                float sum[VEC];
-                load_vec<VEC>(my_hacc, sum);
-                if (!mg) extend(h, sum);
-                float *dst = acc + h * R + k * VEC;
-                add_vec<VEC>(sum, dst);
-                store_vec<VEC>(dst, sum);
+                float *dst = acc + crow * R + k * VEC;
+                add_vec<VEC>(racc, dst);
+                store_vec<VEC>(dst, racc);
             }
-            if (mg) {
-                const u32 tr = trow[grp];
-                float sum[VEC];
-                load_vec<VEC>(my_tacc, sum);
-                extend(tr, sum);
-                float *dst = acc + tr * R + k * VEC;
-                add_vec<VEC>(sum, dst);
-                store_vec<VEC>(dst, sum);
-            }
+            // the next tile's slices may hold this row: their adds wait here
+            __syncthreads();
         }
-
-        // the next tile's slices may hold any of these rows: their adds wait here
-        __syncthreads();
         // end of the shard: its super-shard's rows to the output (the only shard of
         // its super-shard) or to the shard's row block, and the accumulator back to zero
         if (flags & kTileLast) {

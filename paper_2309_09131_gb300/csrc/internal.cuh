@@ -164,7 +164,7 @@ constexpr int kBlocksPerSM = FLYCOO_BLOCKS_PER_SM;
 // nonzeros of a 3-mode tensor whose factor-row gathers one thread group issues
 // together (each step of the fused kernel's inner loop)
 #ifndef FLYCOO_UNROLL3
-#define FLYCOO_UNROLL3 4
+#define FLYCOO_UNROLL3 3
 #endif
 
 inline int elem_words_for(int N) { return (N + 1 <= 4) ? 4 : 8; }
