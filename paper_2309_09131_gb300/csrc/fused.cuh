@@ -139,6 +139,14 @@ __device__ __forceinline__ void widen(const uint4 &v, float *f) {
     }
 }
 
+// a remapped nonzero: written once and not read again in this pass, so it is
+// kept out of L1, where the factor rows being gathered live
+__device__ __forceinline__ void st_no_l1(uint4 *p, const uint4 v) {
+    asm volatile("st.global.L1::no_allocate.v4.u32 [%0], {%1, %2, %3, %4};" ::"l"(p), "r"(v.x), "r"(v.y), "r"(v.z),
+                 "r"(v.w)
+                 : "memory");
+}
+
 template <int VEC>
 __device__ __forceinline__ void store_vec(float *dst, const float *v) {
 #pragma unroll
@@ -277,7 +285,7 @@ __global__ void __launch_bounds__(256, kBlocksPerSM) fused_mttkrp_remap_kernel(c
                 const size_t dst = snext[i];
 #pragma unroll
                 for (int c = 0; c < C::EQ; ++c)
-                    eout[dst * C::EQ + c] = make_uint4(r[4 * c], r[4 * c + 1], r[4 * c + 2], r[4 * c + 3]);
+                    st_no_l1(eout + dst * C::EQ + c, make_uint4(r[4 * c], r[4 * c + 1], r[4 * c + 2], r[4 * c + 3]));
             }
         }
 
