@@ -46,7 +46,7 @@ def parse_args(argv=None):
     ap.add_argument("--no-bf16", action="store_true")
     ap.add_argument("--no-als", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--cpu-sample", type=int, default=8_000_000, help="nonzeros in the CPU baseline sample")
+    ap.add_argument("--cpu-sample", type=int, default=40_000_000, help="nonzeros in the CPU baseline sample")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
