@@ -4,7 +4,7 @@
  * The library computes sparse MTTKRP (spMTTKRP) for every mode of an N-mode
  * sparse tensor held in the FLYCOO format, and remaps the tensor to the next
  * mode's shard order inside the same pass (Wijeratne, Kannan, Prasanna,
- * "Dynasor", arXiv 2309.09131: Section II-B, Section III, Algorithm 2).
+ * "Dynasor", arXiv 2309.09131: Section II-C, Section III, Algorithm 2).
  *
  * Conventions for every entry point:
  *  - Pointers named d_* are DEVICE pointers on the handle's device; pointers
@@ -56,7 +56,7 @@ typedef enum {
  *  m[n]  super-shard width of mode n: super-shard j holds the nonzeros whose
  *        mode-n index lies in [j*m[n], (j+1)*m[n]).  At most 128: the fused
  *        kernel keeps a super-shard's m[n] output rows in shared memory (the
- *        cache budget of Eq. 2).  Default min(I_n, 128).
+ *        cache budget of Eq. 3).  Default min(I_n, 128).
  *  g     shard size in nonzeros: each super-shard is cut into runs of g
  *        consecutive nonzeros (the last one shorter).  Default: the largest
  *        power of two in [1024, 32768] that leaves about four shards per bin.

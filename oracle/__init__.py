@@ -99,7 +99,7 @@ def factors_f64(factors: Sequence[np.ndarray], bf16: bool = False) -> List[np.nd
 
 
 def mttkrp(idx, vals, factors, mode: int, dims=None) -> np.ndarray:
-    """spMTTKRP of ``mode`` (Section II-B; elementwise equation of Section IV).
+    """spMTTKRP of ``mode`` (Section II-C; the elementwise equation of Section IV, Eq. 4).
 
     ``factors`` are ``[I_w, R]`` arrays (float64 after exact widening); the
     factor of ``mode`` itself is not read.  Returns ``[I_mode, R]`` float64.

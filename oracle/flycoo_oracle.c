@@ -6,7 +6,7 @@
  * header, table or helper with the CUDA library; it is written directly from
  * the paper (Wijeratne, Kannan, Prasanna, "Dynasor", arXiv 2309.09131):
  *
- *   - the elementwise spMTTKRP update (Section II-B and the elementwise
+ *   - the elementwise spMTTKRP update (Section II-C and the elementwise
  *     equation of Section IV): M_n[c_n, r] += val * prod_{w != n} Y_w[c_w, r];
  *   - the FLYCOO partition (Section III-A): super-shards are intervals of m_n
  *     output indices, shards are runs of g elements inside a super-shard;
@@ -22,7 +22,7 @@
 #include <string.h>
 
 /* ------------------------------------------------------------------------ */
-/* spMTTKRP, Section II-B (steps 1-8) and the elementwise equation of        */
+/* spMTTKRP, Section II-C (steps 1-8) and the elementwise equation of        */
 /* Section IV: for every nonzero x = (c_0..c_{N-1}, val):                    */
 /*   l = 1;  for w != n: l = l * Y_w[c_w, :];   M_n[c_n, :] += val * l.       */
 /* Rows of M_n that no nonzero touches stay 0 (Algorithm 2 zeroes Y^_n).     */

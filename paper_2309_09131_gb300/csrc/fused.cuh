@@ -11,7 +11,7 @@
 //
 // Work decomposition.  Thread block b walks the shards that Algorithm 3 put in
 // bin b.  A shard's super-shard owns m_n output rows, which the block
-// accumulates in shared memory (the paper keeps them in cache, Eq. 2).  One
+// accumulates in shared memory (the paper keeps them in cache, Eq. 3).  One
 // elected thread streams the shard's layout tiles (512 nonzeros) into a
 // double-buffered shared-memory stage with 1-D TMA bulk copies (cp.async.bulk
 // on an mbarrier), one tile ahead.  For each tile:

@@ -1,4 +1,4 @@
-"""Pins of the oracle's spMTTKRP (Section II-B; elementwise equation of
+"""Pins of the oracle's spMTTKRP (Section II-C; elementwise equation of
 Section IV) to results fixed by mathematics, not by the oracle itself."""
 import os
 
