@@ -240,9 +240,15 @@ flycoo_status flycoo_cp_als_step(flycoo_handle h, void *const *h_factors, flycoo
 /* ------------------------------------------------------------------------ */
 flycoo_status flycoo_remap(flycoo_handle h, int next_mode, flycoo_stream_t stream);
 
-/* Wait for `stream`, then report device-side failures since the last call:  */
+/* Wait for `stream`, then report device-side failures since the last check: */
 /* FLYCOO_ERR_TIMEOUT if a bounded device wait (on a tile-load barrier) gave  */
 /* up; the flag is cleared.  The kernels never trap: this is how they report.  */
+/* A block that gives up lets its own copies in flight land (bounded) and     */
+/* returns, so the GPU context stays usable.  If a remapping pass was among   */
+/* the work checked, the handle's layout is undefined from then on: every     */
+/* later call that uses the layout returns FLYCOO_ERR_LAYOUT (recreate the    */
+/* handle).  flycoo_cp_als_step and flycoo_cpopt_grad (with h_loss) make the  */
+/* same check before they return.                                            */
 flycoo_status flycoo_sync(flycoo_handle h, flycoo_stream_t stream);
 
 /* Fill *out with the handle's sizes and parameters. */
@@ -291,6 +297,22 @@ flycoo_status flycoo_timing_read(flycoo_handle h, double *h_ms, uint64_t *h_laun
 
 /* Message of the last failed call on this thread ("" if none). */
 const char *flycoo_last_error(void);
+
+/* ------------------------------------------------------------------------ */
+/* Test hooks for the failure paths (no counterpart in the paper).           */
+/* ------------------------------------------------------------------------ */
+
+/* Polls of a tile-load barrier before a fused pass of this handle gives up: */
+/* `polls` >= 0 sets the limit (0 gives up at the first tile without        */
+/* polling), negative restores the default (2^24 polls).  The drain of the   */
+/* copies in flight after giving up keeps the default bound.  Errors:        */
+/* INVALID_ARG.                                                              */
+flycoo_status flycoo_debug_set_wait_limit(flycoo_handle h, int64_t polls);
+
+/* Process-wide: the next `n` device allocations of the library succeed and  */
+/* the one after fails with FLYCOO_ERR_OOM (then every later one, until the  */
+/* hook is reset); negative switches the hook off.  Not thread-safe.        */
+flycoo_status flycoo_debug_fail_alloc_after(int64_t n);
 
 #ifdef __cplusplus
 }

@@ -10,6 +10,8 @@ from ._native import (  # noqa: F401
     FlycooError,
     flycoo_cp_als_step,
     flycoo_cpopt_grad,
+    flycoo_debug_fail_alloc_after,
+    flycoo_debug_set_wait_limit,
     flycoo_create,
     flycoo_destroy,
     flycoo_export_layout,

@@ -76,6 +76,8 @@ def lib():
             "flycoo_timing_enable": [P, I],
             "flycoo_timing_read": [P, P, P],
             "flycoo_last_error": [],
+            "flycoo_debug_set_wait_limit": [P, ctypes.c_int64],
+            "flycoo_debug_fail_alloc_after": [ctypes.c_int64],
         }
         for name, args in sigs.items():
             fn = getattr(L, name)
@@ -252,6 +254,16 @@ def flycoo_cp_als_step(h, factors: Sequence[torch.Tensor], lam: torch.Tensor, st
     _check(lib().flycoo_cp_als_step(h, F, BF16 if dt == torch.bfloat16 else F32, int(R), Lp, ctypes.byref(fit),
                                     _stream(stream)))
     return fit.value
+
+
+def flycoo_debug_set_wait_limit(h, polls: int) -> None:
+    """Test hook: barrier polls before a fused pass gives up (negative = default)."""
+    _check(lib().flycoo_debug_set_wait_limit(h, int(polls)))
+
+
+def flycoo_debug_fail_alloc_after(n: int) -> None:
+    """Test hook: the allocation after the next ``n`` fails (negative = off)."""
+    _check(lib().flycoo_debug_fail_alloc_after(int(n)))
 
 
 def flycoo_remap(h, next_mode: int, stream=None) -> None:

@@ -395,6 +395,7 @@ flycoo_status als_step(Tensor &t, void *const *F, flycoo_dtype fdt, int R, doubl
     while (t.layout != 0) {
         FLY_TRY(launch_remap_step(t, t.layout, t.elem[t.cur].p, t.elem[1 - t.cur].p, s));
         t.cur = 1 - t.cur;
+        t.remap_since_sync = true;
         t.layout = (t.layout + 1) % N;
     }
     if (!w.normx2_valid) {
@@ -440,7 +441,7 @@ flycoo_status als_step(Tensor &t, void *const *F, flycoo_dtype fdt, int R, doubl
     FLY_TRY_CUDA(cudaGetLastError());
     double res[3];
     FLY_TRY_CUDA(cudaMemcpyAsync(res, scal, sizeof(res), cudaMemcpyDeviceToHost, s));
-    FLY_TRY_CUDA(cudaStreamSynchronize(s));
+    FLY_TRY(check_error_word(t, s, "flycoo_cp_als_step"));
     u32 st;
     memcpy(&st, &res[2], sizeof(st));
     if (st) {

@@ -88,6 +88,38 @@ static flycoo_status upload(DevBuf &d, const std::vector<T> &h, cudaStream_t s) 
 
 // Section III-A pointers of one mode from its super-shard pointers, plus the
 // super-shard of every shard, both schedules and the K4 work list.
+long long g_alloc_fail_after = -1;
+
+// a handle whose remapping pass gave up has an undefined layout
+flycoo_status check_usable(const Tensor &t, const char *who) {
+    if (t.poisoned) {
+        set_error("%s: a remapping pass on this handle gave up (FLYCOO_ERR_TIMEOUT), so its layout is "
+                  "undefined; destroy the handle and create it again", who);
+        return FLYCOO_ERR_LAYOUT;
+    }
+    return FLYCOO_OK;
+}
+
+// reads and clears the device error word (waits for the stream); TIMEOUT if a
+// bounded device wait gave up since the last check
+flycoo_status check_error_word(Tensor &t, cudaStream_t s, const char *who) {
+    u32 e = 0;
+    FLY_TRY_CUDA(cudaMemcpyAsync(&e, t.err.p, sizeof(u32), cudaMemcpyDeviceToHost, s));
+    FLY_TRY_CUDA(cudaStreamSynchronize(s));
+    const bool remapped = t.remap_since_sync;
+    t.remap_since_sync = false;
+    if (e) {
+        FLY_TRY_CUDA(cudaMemsetAsync(t.err.p, 0, sizeof(u32), s));
+        FLY_TRY_CUDA(cudaStreamSynchronize(s));
+        if (remapped) t.poisoned = true;
+        set_error("%s: a bounded device wait gave up (error word 0x%x)%s", who, e,
+                  remapped ? "; a remapping pass was among the failed work, so the handle's layout is undefined"
+                           : "");
+        return FLYCOO_ERR_TIMEOUT;
+    }
+    return FLYCOO_OK;
+}
+
 flycoo_status partition_mode(Tensor &t, int n, const std::vector<u32> &ssp, cudaStream_t s) {
     ModeMeta &md = t.mode[n];
     const u64 I = t.dims[n];
@@ -231,6 +263,7 @@ extern "C" flycoo_status flycoo_create(int N, const uint64_t *h_dims, uint64_t n
     t->nnz = nnz;
     for (int w = 0; w < N; ++w) t->dims[w] = h_dims[w];
     t->bins = (params && params->bins) ? params->bins : (u32)(kBlocksPerSM * t->sm_count);
+    t->wait_limit = kSpinLimit;
     if (params && params->g) {
         t->g = params->g;
     } else {
@@ -330,6 +363,7 @@ extern "C" flycoo_status flycoo_spmttkrp(flycoo_handle h, int mode, const void *
         return FLYCOO_ERR_LAYOUT;
     }
     DeviceGuard dg(t.device);
+    FLY_TRY(check_usable(t, "flycoo_spmttkrp"));
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const ModeMeta &md = t.mode[mode];
     if (t.nnz == 0) {
@@ -358,6 +392,7 @@ extern "C" flycoo_status flycoo_spmttkrp(flycoo_handle h, int mode, const void *
     a.m = (u32)md.m;
     a.S = (u32)md.S;
     a.bins = t.bins;
+    a.wait_limit = t.wait_limit;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (t.timing) {
         FLY_TRY(next_event_pair(t, &e0, &e1));
@@ -379,6 +414,7 @@ extern "C" flycoo_status flycoo_spmttkrp(flycoo_handle h, int mode, const void *
     FLY_TRY(launch_fixup(R, f, s));
     if (next_mode >= 0) {
         t.cur = 1 - t.cur;
+        t.remap_since_sync = true;
         t.layout = next_mode;
     }
     return FLYCOO_OK;
@@ -392,16 +428,7 @@ extern "C" flycoo_status flycoo_sync(flycoo_handle h, flycoo_stream_t stream) {
     }
     DeviceGuard dg(h->device);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    u32 e = 0;
-    FLY_TRY_CUDA(cudaMemcpyAsync(&e, h->err.p, sizeof(u32), cudaMemcpyDeviceToHost, s));
-    FLY_TRY_CUDA(cudaStreamSynchronize(s));
-    if (e) {
-        FLY_TRY_CUDA(cudaMemsetAsync(h->err.p, 0, sizeof(u32), s));
-        FLY_TRY_CUDA(cudaStreamSynchronize(s));
-        set_error("flycoo_sync: a bounded device wait gave up (error word 0x%x)", e);
-        return FLYCOO_ERR_TIMEOUT;
-    }
-    return FLYCOO_OK;
+    return check_error_word(*h, s, "flycoo_sync");
 }
 
 // One fused pass of mode `mode` in its layout: spMTTKRP (Yout == nullptr) or the
@@ -437,6 +464,7 @@ flycoo_status flycoo::run_pass(Tensor &t, int mode, const void *const *F, flycoo
     a.m = (u32)md.m;
     a.S = (u32)md.S;
     a.bins = t.bins;
+    a.wait_limit = t.wait_limit;
     FLY_TRY(launch_fused(t.N, R, fdt, a, s));
     FixupArgs f{};
     f.items = md.d_k4.as<u32>();
@@ -448,6 +476,7 @@ flycoo_status flycoo::run_pass(Tensor &t, int mode, const void *const *F, flycoo
     f.m = a.m;
     FLY_TRY(launch_fixup(R, f, s));
     t.cur = 1 - t.cur;
+    t.remap_since_sync = true;
     t.layout = (mode + 1) % t.N;
     return FLYCOO_OK;
 }
@@ -491,6 +520,7 @@ extern "C" flycoo_status flycoo_mttkrp_adjoint(flycoo_handle h, int mode, const 
             return FLYCOO_ERR_INVALID_ARG;
         }
     DeviceGuard dg(t.device);
+    FLY_TRY(check_usable(t, "flycoo_mttkrp_adjoint"));
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     // the factor list of every pass: Y_w, with the output mode's slot holding G
     std::vector<const void *> F(t.N);
@@ -499,6 +529,7 @@ extern "C" flycoo_status flycoo_mttkrp_adjoint(flycoo_handle h, int mode, const 
     while (t.layout != first) {
         FLY_TRY(launch_remap_step(t, t.layout, t.elem[t.cur].p, t.elem[1 - t.cur].p, s));
         t.cur = 1 - t.cur;
+        t.remap_since_sync = true;
         t.layout = (t.layout + 1) % t.N;
     }
     for (int q = 1; q < t.N; ++q) {
@@ -508,6 +539,7 @@ extern "C" flycoo_status flycoo_mttkrp_adjoint(flycoo_handle h, int mode, const 
         } else {
             FLY_TRY(launch_remap_step(t, w, t.elem[t.cur].p, t.elem[1 - t.cur].p, s));
             t.cur = 1 - t.cur;
+            t.remap_since_sync = true;
             t.layout = (w + 1) % t.N;
         }
     }
@@ -533,6 +565,7 @@ extern "C" flycoo_status flycoo_cpopt_grad(flycoo_handle h, const float *const *
             return FLYCOO_ERR_INVALID_ARG;
         }
     DeviceGuard dg(t.device);
+    FLY_TRY(check_usable(t, "flycoo_cpopt_grad"));
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const void *const *F = reinterpret_cast<const void *const *>(h_factors);
     double *lp = t.loss_part.as<double>();
@@ -546,7 +579,7 @@ extern "C" flycoo_status flycoo_cpopt_grad(flycoo_handle h, const float *const *
         std::vector<double> part(t.bins, 0.0);
         if (t.nnz)
             FLY_TRY_CUDA(cudaMemcpyAsync(part.data(), lp, (size_t)t.bins * sizeof(double), cudaMemcpyDeviceToHost, s));
-        FLY_TRY_CUDA(cudaStreamSynchronize(s));
+        FLY_TRY(check_error_word(t, s, "flycoo_cpopt_grad"));
         double L = 0.0;
         for (double x : part) L += x; // fixed order
         *h_loss = L;
@@ -572,6 +605,7 @@ extern "C" flycoo_status flycoo_cp_als_step(flycoo_handle h, void *const *h_fact
         return FLYCOO_ERR_INVALID_ARG;
     }
     DeviceGuard dg(t.device);
+    FLY_TRY(check_usable(t, "flycoo_cp_als_step"));
     return als_step(t, h_factors, fdt, R, d_lambda, h_fit, reinterpret_cast<cudaStream_t>(stream));
 }
 
@@ -583,10 +617,12 @@ extern "C" flycoo_status flycoo_remap(flycoo_handle h, int next_mode, flycoo_str
     }
     Tensor &t = *h;
     DeviceGuard dg(t.device);
+    FLY_TRY(check_usable(t, "flycoo_remap"));
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     while (t.layout != next_mode) {
         FLY_TRY(launch_remap_step(t, t.layout, t.elem[t.cur].p, t.elem[1 - t.cur].p, s));
         t.cur = 1 - t.cur;
+        t.remap_since_sync = true;
         t.layout = (t.layout + 1) % t.N;
     }
     return FLYCOO_OK;
@@ -626,6 +662,7 @@ extern "C" flycoo_status flycoo_export_layout(flycoo_handle h, uint32_t *d_idx_o
         return FLYCOO_ERR_INVALID_ARG;
     }
     DeviceGuard dg(h->device);
+    FLY_TRY(check_usable(*h, "flycoo_export_layout"));
     return launch_export_layout(*h, h->elem[h->cur].p, d_idx_out, d_vals_out,
                                 reinterpret_cast<cudaStream_t>(stream));
 }
@@ -704,5 +741,21 @@ extern "C" flycoo_status flycoo_timing_read(flycoo_handle h, double *h_ms, uint6
     if (h_launches) *h_launches = h->ev_pending.size();
     h->ev_pending.clear();
     h->ev_used = 0;
+    return FLYCOO_OK;
+}
+
+extern "C" flycoo_status flycoo_debug_set_wait_limit(flycoo_handle h, int64_t polls) {
+    clear_error();
+    if (!h) {
+        set_error("flycoo_debug_set_wait_limit: handle is NULL");
+        return FLYCOO_ERR_INVALID_ARG;
+    }
+    h->wait_limit = polls < 0 ? kSpinLimit : (u32)std::min<int64_t>(polls, kSpinLimit);
+    return FLYCOO_OK;
+}
+
+extern "C" flycoo_status flycoo_debug_fail_alloc_after(int64_t n) {
+    clear_error();
+    g_alloc_fail_after = n < 0 ? -1 : n;
     return FLYCOO_OK;
 }

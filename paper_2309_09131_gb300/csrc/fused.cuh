@@ -114,9 +114,9 @@ __device__ __forceinline__ void tma_load_1d(void *dst, const void *src, u32 byte
                  : "memory");
 }
 
-// bounded wait; true on success
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, u32 parity) {
-    for (u32 i = 0; i < kSpinLimit; ++i)
+// bounded wait (at most `limit` polls); true on success
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, u32 parity, u32 limit = kSpinLimit) {
+    for (u32 i = 0; i < limit; ++i)
         if (mbar_try_wait(bar, parity)) return true;
     return false;
 }
@@ -257,10 +257,13 @@ __global__ void __launch_bounds__(256, kBlocksPerSM) fused_mttkrp_remap_kernel(c
     for (u32 q = 0; q < ntile; ++q) {
         const int st = q & 1;
         // warp-uniform, so the warp-collective code below runs with every lane or none
-        const bool timed_out = __any_sync(0xffffffffu, !mbar_wait_bounded(&bar[st], (q >> 1) & 1u));
+        const bool timed_out = __any_sync(0xffffffffu, !mbar_wait_bounded(&bar[st], (q >> 1) & 1u, a.wait_limit));
+        // the descriptor is valid only after a successful wait (it is published by
+        // the arrive that the wait acquires); a tile that gave up uses length 1 and
+        // touches no global memory, so every index below stays inside the stage
         const uint4 d = sdesc[st];
         const u32 tstart = d.x;
-        const u32 tlen = d.y & 0xffffu;
+        const u32 tlen = timed_out ? 1u : min(d.y & 0xffffu, (u32)CAP);
         const u32 flags = d.y >> 16;
         const u32 row_base = d.z * a.m;
         const u32 m_eff = min(a.m, a.I_out - row_base);
@@ -410,11 +413,18 @@ __global__ void __launch_bounds__(256, kBlocksPerSM) fused_mttkrp_remap_kernel(c
                 store_vec<VEC>(dst, racc);
             }
         }
-        const int nsync = __syncthreads_count(timed_out ? 1024 : (chain_start && k == 0 ? 1 : 0));
-        if (nsync >= 1024) {
+        // one barrier reports both: every lane of a warp that gave up counts (32 per
+        // warp), and lane 0 of a warp holding a chain start counts once (at most
+        // C::WARPS < 32), so count >= 32 means a wait gave up and count > 0 that
+        // step 3 has work
+        static_assert(C::WARPS < 32, "the barrier count encoding needs fewer than 32 warps");
+        const bool warp_chain = __any_sync(0xffffffffu, chain_start);
+        const int nsync = __syncthreads_count(timed_out || (lane == 0 && warp_chain));
+        if (nsync >= 32) {
             if (tid == 0) {
                 atomicOr(a.err, 1u);
-                // let the copies still in flight land before the block's shared memory is released
+                // let the copies still in flight land before the block's shared memory is
+                // released (always with the full bound, whatever a.wait_limit is)
                 mbar_wait_bounded(&bar[st], (q >> 1) & 1u);
                 if (q + 1 < ntile) mbar_wait_bounded(&bar[st ^ 1], ((q + 1) >> 1) & 1u);
             }

@@ -38,6 +38,10 @@ void clear_error();
     } while (0)
 
 // Owning device allocation (freed on destruction).
+// test hook: the number of device allocations that still succeed before one
+// fails with FLYCOO_ERR_OOM; negative = never (flycoo_debug_fail_alloc_after)
+extern long long g_alloc_fail_after;
+
 struct DevBuf {
     void *p = nullptr;
     size_t bytes = 0;
@@ -53,6 +57,11 @@ struct DevBuf {
     flycoo_status alloc(size_t n) {
         release();
         if (n == 0) n = 16;
+        if (g_alloc_fail_after == 0) {
+            set_error("cudaMalloc(%zu) refused by the allocation-failure test hook", n);
+            return FLYCOO_ERR_OOM;
+        }
+        if (g_alloc_fail_after > 0) --g_alloc_fail_after;
         cudaError_t e = cudaMalloc(&p, n);
         if (e != cudaSuccess) {
             p = nullptr;
@@ -124,6 +133,9 @@ struct Tensor {
     DevBuf partials;    // max_S x max_rows x kMaxRank floats: one row block per shard
     DevBuf err;         // device error word: bit 0 = a bounded device wait gave up
     DevBuf loss_part;   // bins doubles: per-block CP-OPT loss partials
+    u32 wait_limit = 0;            // mbarrier polls before a fused pass gives up (set by create)
+    bool remap_since_sync = false; // a remapping pass was enqueued since the last error-word check
+    bool poisoned = false;         // a remapping pass gave up: the layout is undefined
     AlsWork als;
     ModeMeta mode[FLYCOO_MAX_MODES];
     // kernel timing
@@ -211,6 +223,7 @@ struct FusedArgs {
     u32 m;                     // super-shard width of the output mode
     u32 S;
     u32 bins;
+    u32 wait_limit;            // polls of a tile's barrier before the pass gives up
 };
 
 struct FixupArgs {
@@ -228,6 +241,10 @@ flycoo_status launch_fused(int N, int R, flycoo_dtype dt, const FusedArgs &a, cu
 // spMTTKRP into d_out, or with Yout set the CP-OPT gradient pass (api.cu)
 flycoo_status run_pass(Tensor &t, int mode, const void *const *F, flycoo_dtype fdt, int R, float *d_out,
                        const void *Yout, double *loss_part, cudaStream_t s);
+// handle checks (api.cu): not poisoned by a failed remapping pass / the device
+// error word (waits for the stream; TIMEOUT when a bounded wait gave up)
+flycoo_status check_usable(const Tensor &t, const char *who);
+flycoo_status check_error_word(Tensor &t, cudaStream_t s, const char *who);
 // K7/K8: one CP-ALS iteration, modes 0..N-1, from layout L_0 (als.cu)
 flycoo_status als_step(Tensor &t, void *const *F, flycoo_dtype fdt, int R, double *d_lambda, double *h_fit,
                        cudaStream_t s);

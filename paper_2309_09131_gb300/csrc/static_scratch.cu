@@ -115,6 +115,7 @@ extern "C" flycoo_status flycoo_spmttkrp_static_scratch(flycoo_handle h, int mod
         return FLYCOO_ERR_INVALID_ARG;
     }
     ScratchDeviceGuard dg(t.device);
+    FLY_TRY(check_usable(t, "flycoo_spmttkrp_static_scratch"));
     float *scratch = nullptr;
     FLY_TRY(static_scratch_address(t.device, &scratch));
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
@@ -144,6 +145,7 @@ extern "C" flycoo_status flycoo_spmttkrp_static_scratch(flycoo_handle h, int mod
     a.m = (u32)md.m;
     a.S = (u32)md.S;
     a.bins = t.bins;
+    a.wait_limit = t.wait_limit;
     FLY_TRY(launch_fused(t.N, R, fdt, a, s));
     FixupArgs f{};
     f.items = md.d_k4.as<u32>();
@@ -156,6 +158,7 @@ extern "C" flycoo_status flycoo_spmttkrp_static_scratch(flycoo_handle h, int mod
     FLY_TRY(launch_fixup(R, f, s));
     if (next_mode >= 0) {
         t.cur = 1 - t.cur;
+        t.remap_since_sync = true;
         t.layout = next_mode;
     }
     return FLYCOO_OK;
