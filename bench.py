@@ -45,6 +45,9 @@ def parse_args(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-bf16", action="store_true")
     ap.add_argument("--no-als", action="store_true")
+    ap.add_argument("--no-cpopt", action="store_true")
+    ap.add_argument("--ablations", action="store_true",
+                    help="also time passes without the fused remap and the sweep at R = 16, 32, 64")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=40_000_000, help="nonzeros in the CPU baseline sample")
     args = ap.parse_args(argv)
@@ -243,7 +246,7 @@ def main(argv=None):
             dist.barrier()
 
     import paper_2309_09131_gb300 as P
-    from synth import WORKLOADS, make_workload
+    from synth import WORKLOADS, make_factors, make_workload
 
     wl = WORKLOADS[args.workload]
     t0 = time.perf_counter()
@@ -332,7 +335,8 @@ def main(argv=None):
     # ---- CP-ALS iterations (Algorithm 1 with the least-squares update) on the same tensor
     als = None
     if not args.no_als:
-        Ya = [y.clone() for y in Yf]
+        adt = torch.bfloat16 if wl.factor_dtype == "bf16" else torch.float32
+        Ya = [y.to(adt).clone() for y in Yf]
         lam = torch.empty(R, dtype=torch.float64, device="cuda")
         fits = [T.cp_als_step(Ya, lam)[1] for _ in range(2)]
         torch.cuda.synchronize()
@@ -345,8 +349,66 @@ def main(argv=None):
         ea.record()
         ea.synchronize()
         ms_a = reduce_max(sa.elapsed_time(ea) / iters, world)
-        als = {"ms_per_iter": ms_a, "iters_timed": iters, "spmttkrp_share": step_ms / ms_a,
-               "fits": fits, "factor_dtype": "f32"}
+        sweep_ms = bf16["ms_per_step"] if (adt == torch.bfloat16 and bf16) else step_ms
+        als = {"ms_per_iter": ms_a, "iters_timed": iters, "spmttkrp_share": sweep_ms / ms_a,
+               "fits": fits, "factor_dtype": wl.factor_dtype}
+
+    # ---- CP-OPT loss and gradient sweep (N fused passes forming residuals on the fly), FP32
+    cpopt = None
+    if not args.no_cpopt:
+        grads = [torch.empty_like(y) for y in Yf]
+        loss = P.flycoo_cpopt_grad(T.h, Yf, grads)
+        for _ in range(2):
+            P.flycoo_cpopt_grad(T.h, Yf, grads, want_loss=False)
+        torch.cuda.synchronize()
+        sc = torch.cuda.Event(enable_timing=True)
+        ec = torch.cuda.Event(enable_timing=True)
+        sc.record()
+        for _ in range(args.steps):
+            P.flycoo_cpopt_grad(T.h, Yf, grads, want_loss=False)
+        ec.record()
+        ec.synchronize()
+        cp_b = step_b + sum(wl.dims) * R * 4  # the output mode's own rows are gathered too
+        gbps_c, ms_c = whole_job_gbps(cp_b, sc.elapsed_time(ec) / args.steps, world)
+        cpopt = {"ms_per_sweep": ms_c, "gbps": gbps_c, "loss": loss, "bytes_per_sweep": cp_b}
+
+    # ---- optional: per-mode passes without the fused remap, and other ranks
+    extra = {}
+    if args.ablations:
+        T.remap(0)
+        nr = []
+        for n in range(N):
+            T.remap(n)
+            for _ in range(3):
+                P.flycoo_spmttkrp(T.h, n, Yf, outs[n], -1)
+            torch.cuda.synchronize()
+            s0 = torch.cuda.Event(enable_timing=True)
+            s1 = torch.cuda.Event(enable_timing=True)
+            s0.record()
+            for _ in range(args.steps):
+                P.flycoo_spmttkrp(T.h, n, Yf, outs[n], -1)
+            s1.record()
+            s1.synchronize()
+            nr.append(s0.elapsed_time(s1) / args.steps)
+        T.remap(0)
+        extra["no_remap_ms_per_mode"] = nr
+        ranks = {}
+        for R2 in (16, 32, 64):
+            Y2 = [torch.from_numpy(f).cuda() for f in make_factors(wl.dims, R2, wl.factor_law, seed=wl.seed)]
+            o2 = [torch.empty((d, R2), dtype=torch.float32, device="cuda") for d in wl.dims]
+            for _ in range(2):
+                T.all_modes(Y2, o2)
+            torch.cuda.synchronize()
+            s0 = torch.cuda.Event(enable_timing=True)
+            s1 = torch.cuda.Event(enable_timing=True)
+            s0.record()
+            for _ in range(args.steps):
+                T.all_modes(Y2, o2)
+            s1.record()
+            s1.synchronize()
+            ranks[str(R2)] = s0.elapsed_time(s1) / args.steps
+            del Y2, o2
+        extra["all_mode_ms_by_rank_fp32"] = ranks
 
     # ---- end to end through the public API: pinned host factors in, outputs back out
     e2e = None
@@ -401,7 +463,7 @@ def main(argv=None):
                        "parallelism": "replicas" if world > 1 else "single"},
             "all_mode_ms": step_ms, "per_mode_ms": per_mode_ms, "bytes_per_step": step_b,
             "frac_of_hbm_peak": value / world / peak, "bf16": bf16, "preprocess_ms": create_s * 1e3,
-            "generate_s": gen_s, "cp_als": als, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "generate_s": gen_s, "cp_als": als, "cpopt": cpopt, **extra, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches_per_step * args.steps, "clocks": clk,
         }
         print(json.dumps(line), flush=True)
