@@ -13,8 +13,9 @@
 //   5. lambda_r = column 2-norm (FP64); Y_n = Y / lambda rounded to FP32, then
 //      to BF16 when the factors are stored in BF16;
 //   6. G_n = Y_n^T Y_n from the stored factor.
-// Gram matrices: FP32 products summed over 32 rows, those sums accumulated in
-// FP64 per block and the blocks summed in a fixed order.  After the last mode
+// Gram matrices: FP32 products summed over a block's rows of one staged chunk
+// (64 or 128 rows per thread), those sums accumulated in FP64 per block and the
+// blocks summed in a fixed order.  After the last mode
 //   fit = 1 - sqrt(||X||^2 + ||Xhat||^2 - 2 <X, Xhat>) / ||X||,
 //   ||Xhat||^2 = lambda^T (hadamard_w G_w) lambda,
 //   <X, Xhat>  = sum_r lambda_r sum_i M_{N-1}[i,r] Y_{N-1}[i,r].
@@ -30,7 +31,6 @@ namespace flycoo {
 namespace {
 
 constexpr int kAlsThreads = 256;
-constexpr int kGramRows = 32; // rows whose products are summed in FP32
 
 template <bool BF16> __device__ __forceinline__ float load_factor(const void *Y, u64 i) {
     if constexpr (BF16) return __bfloat162float(static_cast<const __nv_bfloat16 *>(Y)[i]);
@@ -43,31 +43,59 @@ __device__ __forceinline__ void block_rows(u64 I, u64 &lo, u64 &hi) {
     hi = min(lo + per, I);
 }
 
-// partials[b][a*R + c] = sum over the rows of block b of Y[i,a] Y[i,c].
-// Thread t owns the B x B sub-block at rows (t/16)*B, columns (t%16)*B, B = R/16.
+// Gram partials: partials[b][a*R + c] = sum over the rows of block b of Y[i,a] Y[i,c].
+// A block stages chunks of rows (32 KB of FP32) in shared memory with 16-byte
+// loads.  Thread t of row group g owns the B x B tile at (a0, c0) and sums the
+// products of the group's rows of the chunk in FP32; the chunk sums are
+// accumulated in FP64, and the groups' partials are added in group order.
+template <int R> struct GramCfg {
+    static constexpr int B = (R >= 32) ? 4 : 2;      // register tile per thread
+    static constexpr int TB = R / B;                 // tiles per matrix row
+    static constexpr int TPG = TB * TB;              // threads per row group
+    static constexpr int NG = kAlsThreads / TPG;     // row groups
+    static constexpr int ROWS = 8192 / R;            // rows per chunk (32 KB of FP32)
+    static_assert(NG >= 1 && NG * R * R * 8 <= ROWS * R * 4, "group partials must fit the chunk buffer");
+};
+
 template <int R, bool BF16>
 __global__ void __launch_bounds__(kAlsThreads) gram_partial_kernel(const void *Y, u64 I, double *partials) {
-    constexpr int B = R / 16;
-    __shared__ float rows[kGramRows * R];
+    using C = GramCfg<R>;
+    constexpr int B = C::B, NG = C::NG, ROWS = C::ROWS;
+    __shared__ __align__(16) float rows[ROWS * R];
     u64 lo, hi;
     block_rows(I, lo, hi);
-    const int a0 = (threadIdx.x / 16) * B, c0 = (threadIdx.x % 16) * B;
+    const int g = threadIdx.x / C::TPG, tig = threadIdx.x % C::TPG;
+    const int a0 = (tig / C::TB) * B, c0 = (tig % C::TB) * B;
     double acc[B][B];
 #pragma unroll
     for (int x = 0; x < B; ++x)
 #pragma unroll
         for (int y = 0; y < B; ++y) acc[x][y] = 0.0;
-    for (u64 r0 = lo; r0 < hi; r0 += kGramRows) {
-        const int nr = (int)min((u64)kGramRows, hi - r0);
+    for (u64 r0 = lo; r0 < hi; r0 += ROWS) {
+        const int nr = (int)min((u64)ROWS, hi - r0);
         __syncthreads();
-        for (int e = threadIdx.x; e < nr * R; e += kAlsThreads) rows[e] = load_factor<BF16>(Y, r0 * R + e);
+        if constexpr (BF16) {
+            const uint4 *src = reinterpret_cast<const uint4 *>(static_cast<const __nv_bfloat16 *>(Y) + r0 * R);
+            for (int e = threadIdx.x; e < nr * R / 8; e += kAlsThreads) {
+                const uint4 v = src[e];
+                const u32 wv[4] = {v.x, v.y, v.z, v.w};
+                float4 *dst = reinterpret_cast<float4 *>(rows + e * 8);
+                dst[0] = make_float4(__uint_as_float(wv[0] << 16), __uint_as_float(wv[0] & 0xffff0000u),
+                                     __uint_as_float(wv[1] << 16), __uint_as_float(wv[1] & 0xffff0000u));
+                dst[1] = make_float4(__uint_as_float(wv[2] << 16), __uint_as_float(wv[2] & 0xffff0000u),
+                                     __uint_as_float(wv[3] << 16), __uint_as_float(wv[3] & 0xffff0000u));
+            }
+        } else {
+            const float4 *src = reinterpret_cast<const float4 *>(static_cast<const float *>(Y) + r0 * R);
+            for (int e = threadIdx.x; e < nr * R / 4; e += kAlsThreads) reinterpret_cast<float4 *>(rows)[e] = src[e];
+        }
         __syncthreads();
-        float s[B][B];
+        float sum[B][B];
 #pragma unroll
         for (int x = 0; x < B; ++x)
 #pragma unroll
-            for (int y = 0; y < B; ++y) s[x][y] = 0.f;
-        for (int i = 0; i < nr; ++i) {
+            for (int y = 0; y < B; ++y) sum[x][y] = 0.f;
+        for (int i = g; i < nr; i += NG) {
             float va[B], vc[B];
 #pragma unroll
             for (int x = 0; x < B; ++x) {
@@ -77,18 +105,26 @@ __global__ void __launch_bounds__(kAlsThreads) gram_partial_kernel(const void *Y
 #pragma unroll
             for (int x = 0; x < B; ++x)
 #pragma unroll
-                for (int y = 0; y < B; ++y) s[x][y] = fmaf(va[x], vc[y], s[x][y]);
+                for (int y = 0; y < B; ++y) sum[x][y] = fmaf(va[x], vc[y], sum[x][y]);
         }
 #pragma unroll
         for (int x = 0; x < B; ++x)
 #pragma unroll
-            for (int y = 0; y < B; ++y) acc[x][y] += (double)s[x][y];
+            for (int y = 0; y < B; ++y) acc[x][y] += (double)sum[x][y];
     }
-    double *o = partials + (size_t)blockIdx.x * R * R;
+    __syncthreads();
+    double *gp = reinterpret_cast<double *>(rows); // [NG][R*R]
 #pragma unroll
     for (int x = 0; x < B; ++x)
 #pragma unroll
-        for (int y = 0; y < B; ++y) o[(a0 + x) * R + c0 + y] = acc[x][y];
+        for (int y = 0; y < B; ++y) gp[g * R * R + (a0 + x) * R + c0 + y] = acc[x][y];
+    __syncthreads();
+    for (int e = threadIdx.x; e < R * R; e += kAlsThreads) {
+        double t = 0.0;
+#pragma unroll
+        for (int q = 0; q < NG; ++q) t += gp[q * R * R + e];
+        partials[(size_t)blockIdx.x * R * R + e] = t;
+    }
 }
 
 // out[e] = sum over b < nblocks of partials[b * len + e] (sqrt of it with
@@ -207,14 +243,18 @@ __global__ void __launch_bounds__(kInvWarps * 32)
     if (has1) W[i1 * R + c] = (float)z1;
 }
 
-// Y = M W in FP32; thread t computes column c = t % R of rows lo + t/R, stepping
-// by 256/R, with column c of W in registers.  Per-block column sums of squares.
+// Y = M W in FP32.  Tiles of M (16 KB) are staged in shared memory; thread t
+// computes column c = t % R of the tile's rows t/R, t/R + 256/R, ..., with
+// column c of W in registers.  Per-block column sums of squares (FP32 over a
+// tile, FP64 across tiles).
 template <int R>
 __global__ void __launch_bounds__(kAlsThreads)
     als_apply_kernel(const float *M, const float *W, float *Y, u64 I, double *colsq, const u32 *status) {
+    constexpr int ROWS = 4096 / R;
+    constexpr int rstep = kAlsThreads / R;
+    __shared__ __align__(16) float mt[ROWS * R];
     __shared__ double part[kAlsThreads];
     if (*status) return;
-    constexpr int rstep = kAlsThreads / R;
     const int c = threadIdx.x % R, rsub = threadIdx.x / R;
     float w[R];
 #pragma unroll
@@ -222,63 +262,112 @@ __global__ void __launch_bounds__(kAlsThreads)
     u64 lo, hi;
     block_rows(I, lo, hi);
     double sq = 0.0;
-    for (u64 i = lo + rsub; i < hi; i += rstep) {
-        const float4 *m = reinterpret_cast<const float4 *>(M + i * R);
-        float y = 0.f;
+    for (u64 r0 = lo; r0 < hi; r0 += ROWS) {
+        const int nr = (int)min((u64)ROWS, hi - r0);
+        __syncthreads();
+        const float4 *src = reinterpret_cast<const float4 *>(M + r0 * R);
+        for (int e = threadIdx.x; e < nr * R / 4; e += kAlsThreads) reinterpret_cast<float4 *>(mt)[e] = src[e];
+        __syncthreads();
+        float sq32 = 0.f;
+        for (int i = rsub; i < nr; i += rstep) {
+            const float4 *m = reinterpret_cast<const float4 *>(mt + i * R);
+            float y = 0.f;
 #pragma unroll
-        for (int a4 = 0; a4 < R / 4; ++a4) {
-            const float4 v = m[a4];
-            y = fmaf(v.x, w[4 * a4 + 0], y);
-            y = fmaf(v.y, w[4 * a4 + 1], y);
-            y = fmaf(v.z, w[4 * a4 + 2], y);
-            y = fmaf(v.w, w[4 * a4 + 3], y);
+            for (int a4 = 0; a4 < R / 4; ++a4) {
+                const float4 v = m[a4];
+                y = fmaf(v.x, w[4 * a4 + 0], y);
+                y = fmaf(v.y, w[4 * a4 + 1], y);
+                y = fmaf(v.z, w[4 * a4 + 2], y);
+                y = fmaf(v.w, w[4 * a4 + 3], y);
+            }
+            Y[(r0 + i) * R + c] = y;
+            sq32 = fmaf(y, y, sq32);
         }
-        Y[i * R + c] = y;
-        sq += (double)y * (double)y;
+        sq += (double)sq32;
     }
     part[threadIdx.x] = sq;
     __syncthreads();
     if (threadIdx.x < R) {
-        double s = 0.0;
-        for (int q = 0; q < rstep; ++q) s += part[q * R + threadIdx.x];
-        colsq[(size_t)blockIdx.x * R + threadIdx.x] = s;
+        double t = 0.0;
+        for (int q = 0; q < rstep; ++q) t += part[q * R + threadIdx.x];
+        colsq[(size_t)blockIdx.x * R + threadIdx.x] = t;
     }
 }
 
 // factor = Y * (1 / lambda) in FP64, rounded to FP32, then to BF16 when stored
-// so; with M set, also the per-block partials of sum_i M[i,r] factor[i,r]
-template <bool BF16>
+// so; with M set, also the per-block partials of sum_i M[i,r] factor[i,r].
+// Thread t handles the four columns 4q..4q+3, q = t % (R/4), of every
+// (256/(R/4))-th row, with 16-byte loads.
+template <int R, bool BF16>
 __global__ void __launch_bounds__(kAlsThreads)
-    normalize_store_kernel(const float *Yt, const double *lambda, void *Yout, u64 I, int R, const float *M,
-                           double *inner, const u32 *status) {
-    __shared__ double part[kAlsThreads];
+    normalize_store_kernel(const float *Yt, const double *lambda, void *Yout, u64 I, const float *M, double *inner,
+                           const u32 *status) {
+    constexpr int Q = R / 4;
+    constexpr int rstep = kAlsThreads / Q;
+    __shared__ double part[4][kAlsThreads];
     if (*status) return;
-    const int rstep = kAlsThreads / R;
-    const int c = threadIdx.x % R, rsub = threadIdx.x / R;
-    const double lam = lambda[c];
-    const double inv = lam > 0.0 ? 1.0 / lam : 1.0;
+    const int q = threadIdx.x % Q, rsub = threadIdx.x / Q;
+    double inv[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const double lam = lambda[4 * q + j];
+        inv[j] = lam > 0.0 ? 1.0 / lam : 1.0;
+    }
     u64 lo, hi;
     block_rows(I, lo, hi);
-    double s = 0.0;
+    double s[4] = {0.0, 0.0, 0.0, 0.0};
     for (u64 i = lo + rsub; i < hi; i += rstep) {
-        float stored = (float)((double)Yt[i * R + c] * inv);
+        const float4 y = reinterpret_cast<const float4 *>(Yt)[i * Q + q];
+        float v[4] = {(float)((double)y.x * inv[0]), (float)((double)y.y * inv[1]), (float)((double)y.z * inv[2]),
+                      (float)((double)y.w * inv[3])};
         if constexpr (BF16) {
-            const __nv_bfloat16 b = __float2bfloat16_rn(stored);
-            static_cast<__nv_bfloat16 *>(Yout)[i * R + c] = b;
-            stored = __bfloat162float(b);
+            __nv_bfloat16 b[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                b[j] = __float2bfloat16_rn(v[j]);
+                v[j] = __bfloat162float(b[j]);
+            }
+            uint2 packed;
+            packed.x = (u32)__bfloat16_as_ushort(b[0]) | ((u32)__bfloat16_as_ushort(b[1]) << 16);
+            packed.y = (u32)__bfloat16_as_ushort(b[2]) | ((u32)__bfloat16_as_ushort(b[3]) << 16);
+            reinterpret_cast<uint2 *>(Yout)[i * Q + q] = packed;
         } else {
-            static_cast<float *>(Yout)[i * R + c] = stored;
+            reinterpret_cast<float4 *>(Yout)[i * Q + q] = make_float4(v[0], v[1], v[2], v[3]);
         }
-        if (M) s += (double)M[i * R + c] * (double)stored;
+        if (M) {
+            const float4 m = reinterpret_cast<const float4 *>(M)[i * Q + q];
+            s[0] += (double)m.x * (double)v[0];
+            s[1] += (double)m.y * (double)v[1];
+            s[2] += (double)m.z * (double)v[2];
+            s[3] += (double)m.w * (double)v[3];
+        }
     }
     if (inner) {
-        part[threadIdx.x] = s;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) part[j][threadIdx.x] = s[j];
         __syncthreads();
         if (threadIdx.x < R) {
+            const int cq = threadIdx.x / 4, cj = threadIdx.x % 4;
             double t = 0.0;
-            for (int q = 0; q < rstep; ++q) t += part[q * R + threadIdx.x];
+            for (int r = 0; r < rstep; ++r) t += part[cj][r * Q + cq];
             inner[(size_t)blockIdx.x * R + threadIdx.x] = t;
         }
+    }
+}
+
+template <int R>
+void launch_normalize_t(bool bf, const float *Yt, const double *lambda, void *Yout, u64 I, const float *M,
+                        double *inner, const u32 *status, int nblk, cudaStream_t s) {
+    if (bf) normalize_store_kernel<R, true><<<nblk, kAlsThreads, 0, s>>>(Yt, lambda, Yout, I, M, inner, status);
+    else normalize_store_kernel<R, false><<<nblk, kAlsThreads, 0, s>>>(Yt, lambda, Yout, I, M, inner, status);
+}
+
+void launch_normalize(int R, bool bf, const float *Yt, const double *lambda, void *Yout, u64 I, const float *M,
+                      double *inner, const u32 *status, int nblk, cudaStream_t s) {
+    switch (R) {
+    case 16: launch_normalize_t<16>(bf, Yt, lambda, Yout, I, M, inner, status, nblk, s); break;
+    case 32: launch_normalize_t<32>(bf, Yt, lambda, Yout, I, M, inner, status, nblk, s); break;
+    default: launch_normalize_t<64>(bf, Yt, lambda, Yout, I, M, inner, status, nblk, s); break;
     }
 }
 
@@ -373,7 +462,7 @@ flycoo_status als_step(Tensor &t, void *const *F, flycoo_dtype fdt, int R, doubl
     AlsWork &w = t.als;
     u64 maxI = 0;
     for (int n = 0; n < N; ++n) maxI = std::max<u64>(maxI, t.dims[n]);
-    const int nblk = 2 * t.sm_count;
+    const int nblk = 4 * t.sm_count;
     if (w.rows < maxI || w.nblk != nblk) {
         FLY_TRY(w.M.alloc(maxI * kMaxRank * sizeof(float)));
         FLY_TRY(w.Y.alloc(maxI * kMaxRank * sizeof(float)));
@@ -428,12 +517,7 @@ flycoo_status als_step(Tensor &t, void *const *F, flycoo_dtype fdt, int R, doubl
         const bool last = n == N - 1;
         float *Mlast = last ? w.M.as<float>() : nullptr;
         double *inner = last ? w.inner.as<double>() : nullptr;
-        if (bf)
-            normalize_store_kernel<true><<<nblk, kAlsThreads, 0, s>>>(w.Y.as<float>(), d_lambda, F[n], I, R, Mlast,
-                                                                     inner, status);
-        else
-            normalize_store_kernel<false><<<nblk, kAlsThreads, 0, s>>>(w.Y.as<float>(), d_lambda, F[n], I, R, Mlast,
-                                                                      inner, status);
+        launch_normalize(R, bf, w.Y.as<float>(), d_lambda, F[n], I, Mlast, inner, status, nblk, s);
         FLY_TRY_CUDA(cudaGetLastError());
         FLY_TRY(gram(F[n], bf, I, R, G + n * RR, w.gpart.as<double>(), nblk, s));
     }
