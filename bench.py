@@ -409,6 +409,20 @@ def main(argv=None):
             ranks[str(R2)] = s0.elapsed_time(s1) / args.steps
             del Y2, o2
         extra["all_mode_ms_by_rank_fp32"] = ranks
+        # the same sweep with the block-cyclic schedule instead of Algorithm 3 (LPT)
+        Tb = P.FlycooTensor(idx, vals, wl.dims, schedule=P._native.SCHEDULE_BLOCK_CYCLIC)
+        for _ in range(2):
+            Tb.all_modes(Yf, outs)
+        torch.cuda.synchronize()
+        s0 = torch.cuda.Event(enable_timing=True)
+        s1 = torch.cuda.Event(enable_timing=True)
+        s0.record()
+        for _ in range(args.steps):
+            Tb.all_modes(Yf, outs)
+        s1.record()
+        s1.synchronize()
+        extra["all_mode_ms_block_cyclic_schedule"] = s0.elapsed_time(s1) / args.steps
+        Tb.close()
 
     # ---- end to end through the public API: pinned host factors in, outputs back out
     e2e = None

@@ -61,12 +61,18 @@ typedef enum {
  *        consecutive nonzeros (the last one shorter).  Default: the largest
  *        power of two in [1024, 32768] that leaves about four shards per bin.
  *  bins  number of schedule bins of Algorithm 3, which is also the number of
- *        thread blocks of the fused kernel.  Default: 3 x the SM count. */
+ *        thread blocks of the fused kernel.  Default: 3 x the SM count.
+ *  schedule  FLYCOO_SCHEDULE_LPT (0, default): Algorithm 3 -- items sorted by
+ *        size, each to the least-loaded bin; FLYCOO_SCHEDULE_BLOCK_CYCLIC (1):
+ *        item i to bin i mod bins, in ascending order (the baseline the paper
+ *        compares Algorithm 3 with, Section V-D).  Applies to both schedules. */
+#define FLYCOO_SCHEDULE_LPT 0
+#define FLYCOO_SCHEDULE_BLOCK_CYCLIC 1
 typedef struct {
     uint64_t m[FLYCOO_MAX_MODES];
     uint64_t g;
     uint32_t bins;
-    uint32_t reserved;
+    uint32_t schedule;
 } flycoo_params;
 
 /* Read-only description of a handle. */
@@ -79,8 +85,8 @@ typedef struct {
     uint64_t g;                                 /* shard size used                    */
     uint32_t bins;                              /* schedule bins used                 */
     uint32_t elem_bytes;                        /* bytes of one stored nonzero        */
-    uint32_t tile;                              /* layout tile, see flycoo_create     */
-    uint32_t reserved;
+    uint32_t tile;                              /* row-sorted unit, see flycoo_create */
+    uint32_t schedule;                          /* FLYCOO_SCHEDULE_*                  */
     uint64_t super_shards[FLYCOO_MAX_MODES];    /* k_n = ceil(I_n / m_n)              */
     uint64_t shards[FLYCOO_MAX_MODES];          /* S_n = sum_j ceil(|SS_n,j| / g)     */
     uint64_t fixup_super_shards[FLYCOO_MAX_MODES]; /* super-shards without exactly one shard */

@@ -35,14 +35,14 @@ class FlycooError(RuntimeError):
 
 class flycoo_params(ctypes.Structure):
     _fields_ = [("m", ctypes.c_uint64 * MAX_MODES), ("g", ctypes.c_uint64), ("bins", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32)]
+                ("schedule", ctypes.c_uint32)]
 
 
 class flycoo_info(ctypes.Structure):
     _fields_ = [("N", ctypes.c_int32), ("layout_mode", ctypes.c_int32), ("nnz", ctypes.c_uint64),
                 ("dims", ctypes.c_uint64 * MAX_MODES), ("m", ctypes.c_uint64 * MAX_MODES),
                 ("g", ctypes.c_uint64), ("bins", ctypes.c_uint32), ("elem_bytes", ctypes.c_uint32),
-                ("tile", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("tile", ctypes.c_uint32), ("schedule", ctypes.c_uint32),
                 ("super_shards", ctypes.c_uint64 * MAX_MODES), ("shards", ctypes.c_uint64 * MAX_MODES),
                 ("fixup_super_shards", ctypes.c_uint64 * MAX_MODES), ("device_bytes", ctypes.c_uint64)]
 
@@ -116,12 +116,18 @@ def _dev_ptr(t: torch.Tensor, dtypes, what: str) -> ctypes.c_void_p:
     return ctypes.c_void_p(t.data_ptr())
 
 
-def make_params(m: Optional[Sequence[int]] = None, g: int = 0, bins: int = 0) -> flycoo_params:
+SCHEDULE_LPT = 0
+SCHEDULE_BLOCK_CYCLIC = 1
+
+
+def make_params(m: Optional[Sequence[int]] = None, g: int = 0, bins: int = 0,
+                schedule: int = SCHEDULE_LPT) -> flycoo_params:
     p = flycoo_params()
     for i, v in enumerate(m or []):
         p.m[i] = int(v)
     p.g = int(g)
     p.bins = int(bins)
+    p.schedule = int(schedule)
     return p
 
 
@@ -282,7 +288,8 @@ def flycoo_get_info(h) -> dict:
     return dict(N=N, layout_mode=info.layout_mode, nnz=info.nnz, dims=list(info.dims[:N]),
                 m=list(info.m[:N]), g=info.g, bins=info.bins, elem_bytes=info.elem_bytes, tile=info.tile,
                 super_shards=list(info.super_shards[:N]), shards=list(info.shards[:N]),
-                fixup_super_shards=list(info.fixup_super_shards[:N]), device_bytes=info.device_bytes)
+                fixup_super_shards=list(info.fixup_super_shards[:N]), device_bytes=info.device_bytes,
+                schedule=info.schedule)
 
 
 def flycoo_export_layout(h, stream=None):

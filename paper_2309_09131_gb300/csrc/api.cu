@@ -79,6 +79,15 @@ static void lpt_schedule(const std::vector<u64> &size, u32 bins, std::vector<u32
     for (u32 it : order) items[fill[bin_of[it]]++] = it;
 }
 
+// block-cyclic assignment: item i to bin i mod bins, ascending within a bin
+static void block_cyclic_schedule(size_t nitems, u32 bins, std::vector<u32> &bin_ptr, std::vector<u32> &items) {
+    bin_ptr.assign(bins + 1, 0);
+    for (u32 b = 0; b < bins; ++b) bin_ptr[b + 1] = bin_ptr[b] + (u32)(nitems / bins + (b < nitems % bins ? 1 : 0));
+    items.assign(nitems, 0);
+    std::vector<u32> fill(bin_ptr.begin(), bin_ptr.end() - 1);
+    for (size_t i = 0; i < nitems; ++i) items[fill[i % bins]++] = (u32)i;
+}
+
 template <class T>
 static flycoo_status upload(DevBuf &d, const std::vector<T> &h, cudaStream_t s) {
     FLY_TRY(d.alloc(std::max<size_t>(h.size() * sizeof(T), 16)));
@@ -149,8 +158,13 @@ flycoo_status partition_mode(Tensor &t, int n, const std::vector<u32> &ssp, cuda
         for (u64 p = md.shard_ptr[q]; p < md.shard_ptr[q + 1]; p += kSortTile) md.tile_ptr.push_back((u32)p);
     }
     md.tile_ptr.push_back((u32)t.nnz);
-    lpt_schedule(ss_shards, t.bins, md.ss_bin_ptr, md.ss_items);
-    lpt_schedule(shard_size, t.bins, md.sh_bin_ptr, md.sh_items);
+    if (t.schedule == FLYCOO_SCHEDULE_BLOCK_CYCLIC) {
+        block_cyclic_schedule(ss_shards.size(), t.bins, md.ss_bin_ptr, md.ss_items);
+        block_cyclic_schedule(shard_size.size(), t.bins, md.sh_bin_ptr, md.sh_items);
+    } else {
+        lpt_schedule(ss_shards, t.bins, md.ss_bin_ptr, md.ss_items);
+        lpt_schedule(shard_size, t.bins, md.sh_bin_ptr, md.sh_items);
+    }
     // tile descriptors of the block schedule, for both stage-tile sizes
     for (int z = 0; z < 2; ++z) {
         const u32 tile = kStageTile[z];
@@ -264,6 +278,11 @@ extern "C" flycoo_status flycoo_create(int N, const uint64_t *h_dims, uint64_t n
     for (int w = 0; w < N; ++w) t->dims[w] = h_dims[w];
     t->bins = (params && params->bins) ? params->bins : (u32)(kBlocksPerSM * t->sm_count);
     t->wait_limit = kSpinLimit;
+    t->schedule = params ? params->schedule : FLYCOO_SCHEDULE_LPT;
+    if (t->schedule != FLYCOO_SCHEDULE_LPT && t->schedule != FLYCOO_SCHEDULE_BLOCK_CYCLIC) {
+        set_error("flycoo_create: unknown schedule %u", t->schedule);
+        return FLYCOO_ERR_INVALID_ARG;
+    }
     if (params && params->g) {
         t->g = params->g;
     } else {
@@ -643,6 +662,7 @@ extern "C" flycoo_status flycoo_get_info(flycoo_handle h, flycoo_info *out) {
     out->bins = t.bins;
     out->elem_bytes = (uint32_t)(t.elem_words * 4);
     out->tile = kSortTile;
+    out->schedule = t.schedule;
     for (int n = 0; n < t.N; ++n) {
         out->dims[n] = t.dims[n];
         out->m[n] = t.mode[n].m;

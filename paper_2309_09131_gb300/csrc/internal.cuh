@@ -124,6 +124,7 @@ struct Tensor {
     u64 dims[FLYCOO_MAX_MODES] = {};
     u64 g = 0;
     u32 bins = 0;
+    u32 schedule = 0;   // FLYCOO_SCHEDULE_*
     int layout = 0;     // current layout mode
     int elem_words = 4; // 32-bit words per stored nonzero
     int cur = 0;        // which element buffer holds the current layout

@@ -30,15 +30,15 @@ class FlycooTensor:
     """
 
     def __init__(self, idx, vals, dims: Sequence[int], m: Optional[Sequence[int]] = None, g: int = 0,
-                 bins: int = 0, stream=None):
+                 bins: int = 0, stream=None, schedule: int = 0):
         idx_t = _as_cuda(idx, torch.int32)
         vals_t = _as_cuda(vals, torch.float32)
         self.N = int(idx_t.shape[0])
         self.nnz = int(idx_t.shape[1])
         self.dims = [int(d) for d in dims]
         self.h = None
-        self.h = nat.flycoo_create(self.N, self.dims, self.nnz, idx_t, vals_t, nat.make_params(m, g, bins),
-                                   stream)
+        self.h = nat.flycoo_create(self.N, self.dims, self.nnz, idx_t, vals_t,
+                                   nat.make_params(m, g, bins, schedule), stream)
 
     def close(self):
         if self.h:

@@ -225,3 +225,31 @@ def test_error_statuses(P):
     # the context is still usable after the rejected calls
     T.all_modes(facs)
     torch.cuda.synchronize()
+
+
+def test_block_cyclic_schedule(P):
+    # the block-cyclic baseline of Section V-D: item i in bin i mod bins, ascending;
+    # the schedule changes which block does the work, never the result
+    dims = (300, 200, 250)
+    idx, vals = random_coo(dims, 40_000, seed=31, law="zipf")
+    facs = make_factors(dims, 32, "normal", seed=31)
+    bins = 13
+    T = P.FlycooTensor(idx, vals, dims, g=700, bins=bins, schedule=1)
+    info = T.info
+    assert info["schedule"] == 1
+    for mode in range(3):
+        for which, count in ((0, info["super_shards"][mode]), (1, info["shards"][mode])):
+            bp, items = T.export_schedule(mode, which)
+            ref_items = np.concatenate([np.arange(b, count, bins) for b in range(bins)]).astype(np.uint64)
+            ref_bp = np.concatenate([[0], np.cumsum([len(range(b, count, bins)) for b in range(bins)])])
+            np.testing.assert_array_equal(items, ref_items)
+            np.testing.assert_array_equal(bp, ref_bp.astype(np.uint64))
+    Y = [torch.from_numpy(f).cuda() for f in facs]
+    outs = T.all_modes(Y)
+    torch.cuda.synchronize()
+    Y64 = oracle.factors_f64(facs)
+    for n in range(3):
+        assert rel_fro(to_np(outs[n]), oracle.mttkrp(idx, vals, Y64, n, dims)) <= FP32_TOL
+    with pytest.raises(P.FlycooError) as e:
+        P.FlycooTensor(idx, vals, dims, schedule=7)
+    assert e.value.status_name == "FLYCOO_ERR_INVALID_ARG"
