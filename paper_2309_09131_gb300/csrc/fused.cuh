@@ -114,6 +114,46 @@ __device__ __forceinline__ void tma_load_1d(void *dst, const void *src, u32 byte
                  : "memory");
 }
 
+// L2 cache policies.  The pass streams the element buffers (read once, written
+// once) past factor matrices that every nonzero gathers from: the streams are
+// marked evict-first so the factor rows, marked evict-last, stay in L2.
+#ifndef FLYCOO_L2_HINTS
+#define FLYCOO_L2_HINTS 1
+#endif
+__device__ __forceinline__ uint64_t l2_policy_evict_first() {
+    uint64_t p;
+    asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint64_t l2_policy_evict_last() {
+    uint64_t p;
+    asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ void tma_load_1d_hint(void *dst, const void *src, u32 bytes, uint64_t *bar,
+                                                 uint64_t policy) {
+#if FLYCOO_L2_HINTS
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::
+            "r"(smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar)), "l"(policy)
+        : "memory");
+#else
+    tma_load_1d(dst, src, bytes, bar);
+#endif
+}
+__device__ __forceinline__ uint4 ld_factor(const uint4 *p, uint64_t policy) {
+#if FLYCOO_L2_HINTS
+    uint4 v;
+    asm("ld.global.nc.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
+        : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+        : "l"(p), "l"(policy));
+    return v;
+#else
+    return __ldg(p);
+#endif
+}
+
 // bounded wait (at most `limit` polls); true on success
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, u32 parity, u32 limit = kSpinLimit) {
     for (u32 i = 0; i < limit; ++i)
@@ -141,10 +181,16 @@ __device__ __forceinline__ void widen(const uint4 &v, float *f) {
 
 // a remapped nonzero: written once and not read again in this pass, so it is
 // kept out of L1, where the factor rows being gathered live
-__device__ __forceinline__ void st_no_l1(uint4 *p, const uint4 v) {
+__device__ __forceinline__ void st_no_l1(uint4 *p, const uint4 v, uint64_t policy) {
+#if FLYCOO_L2_HINTS
+    asm volatile("st.global.L1::no_allocate.L2::cache_hint.v4.u32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(p), "r"(v.x),
+                 "r"(v.y), "r"(v.z), "r"(v.w), "l"(policy)
+                 : "memory");
+#else
     asm volatile("st.global.L1::no_allocate.v4.u32 [%0], {%1, %2, %3, %4};" ::"l"(p), "r"(v.x), "r"(v.y), "r"(v.z),
                  "r"(v.w)
                  : "memory");
+#endif
 }
 
 template <int VEC>
@@ -218,6 +264,8 @@ __global__ void __launch_bounds__(256, kBlocksPerSM) fused_mttkrp_remap_kernel(c
     const uint4 *Yo = CPOPT ? static_cast<const uint4 *>(a.Yout) + k : nullptr;
     double loss = 0.0;
     float *my_hacc = hacc + grp * R + k * VEC;
+    const uint64_t pol_stream = l2_policy_evict_first();
+    const uint64_t pol_factor = l2_policy_evict_last();
     const uint4 *__restrict__ tiles = a.tiles[C::TZ];
     const u32 t_begin = a.tile_bin_ptr[C::TZ][blockIdx.x];
     const u32 ntile = a.tile_bin_ptr[C::TZ][blockIdx.x + 1] - t_begin;
@@ -245,8 +293,8 @@ __global__ void __launch_bounds__(256, kBlocksPerSM) fused_mttkrp_remap_kernel(c
         sdesc[st] = d;
         fence_proxy_async_smem();
         mbar_arrive_expect_tx(&bar[st], bytes);
-        tma_load_1d(sb, ein + (size_t)start * C::EQ, len * C::EB, &bar[st]);
-        if (remap) tma_load_1d(sb + (size_t)CAP * C::EB, a.next + nlo, (nhi - nlo) * 4u, &bar[st]);
+        tma_load_1d_hint(sb, ein + (size_t)start * C::EQ, len * C::EB, &bar[st], pol_stream);
+        if (remap) tma_load_1d_hint(sb + (size_t)CAP * C::EB, a.next + nlo, (nhi - nlo) * 4u, &bar[st], pol_stream);
     };
     if (tid == 0) {
         if (ntile > 0) issue(0, tiles[t_begin]);
@@ -288,7 +336,8 @@ __global__ void __launch_bounds__(256, kBlocksPerSM) fused_mttkrp_remap_kernel(c
                 const size_t dst = snext[i];
 #pragma unroll
                 for (int c = 0; c < C::EQ; ++c)
-                    st_no_l1(eout + dst * C::EQ + c, make_uint4(r[4 * c], r[4 * c + 1], r[4 * c + 2], r[4 * c + 3]));
+                    st_no_l1(eout + dst * C::EQ + c, make_uint4(r[4 * c], r[4 * c + 1], r[4 * c + 2], r[4 * c + 3]),
+                             pol_stream);
             }
         }
 
@@ -337,8 +386,8 @@ __global__ void __launch_bounds__(256, kBlocksPerSM) fused_mttkrp_remap_kernel(c
 #pragma unroll
             for (int u = 0; u < UU; ++u) {
 #pragma unroll
-                for (int t = 0; t < N - 1; ++t) y[u][t] = __ldg(Yp[t] + (size_t)w[u][t + 1] * RV);
-                if constexpr (CPOPT) y[u][N - 1] = __ldg(Yo + (size_t)w[u][0] * RV);
+                for (int t = 0; t < N - 1; ++t) y[u][t] = ld_factor(Yp[t] + (size_t)w[u][t + 1] * RV, pol_factor);
+                if constexpr (CPOPT) y[u][N - 1] = ld_factor(Yo + (size_t)w[u][0] * RV, pol_factor);
             }
 #pragma unroll
             for (int u = 0; u < UU; ++u) {
