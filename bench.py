@@ -169,6 +169,14 @@ def cpu_oracle_pass(idx, vals, facs, dims, sample):
     return sec, b, S
 
 
+def workload_config(wl):
+    """The workload description both arms report (shape, laws, rank, seed)."""
+    return {"workload": wl.name, "dims": list(wl.dims), "nnz": wl.nnz, "rank": wl.rank,
+            "index_laws": [" ".join(str(x) for x in law) for law in wl.index_laws],
+            "values": wl.value_law, "factor_law": wl.factor_law, "seed": wl.seed,
+            "duplicates": "merged" if wl.distinct else "kept"}
+
+
 def run_reference(args):
     rank, local_rank, world = dist_env()
     if rank != 0:
@@ -188,7 +196,7 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": gbs, "unit": "GB/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": wl.name, "dims": list(wl.dims), "nnz": wl.nnz, "rank": wl.rank},
+        "config": workload_config(wl),
         "cpu_baseline": {"value": gbs, "unit": "GB/s", "cores": 1, "kind": "oracle",
                          "sample": f"first {S} nonzeros (random COO order) of the workload, all "
                                    f"{len(wl.dims)} modes, FP64 single-threaded C oracle, per step"},
@@ -468,12 +476,10 @@ def main(argv=None):
             "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": wl.name, "dims": list(wl.dims), "nnz": wl.nnz, "rank": R,
-                       "factor_dtype": "f32", "index_law": "Zipf(1.1) per mode, duplicates merged",
-                       "values": "lognormal(0,1)", "seed": wl.seed, "g": info["g"], "bins": info["bins"],
+            "config": {**workload_config(wl), "factor_dtype": "f32", "g": info["g"], "bins": info["bins"],
                        "elem_bytes": elem_bytes,
-                       "l2": "no flush: inputs larger than L2 (two 1.23 GB element buffers and 0.92 GB of "
-                             "remap slots streamed per step)",
+                       "l2": f"no flush: inputs larger than L2 (two {wl.nnz * elem_bytes / 1e9:.2f} GB element "
+                             f"buffers and {N * wl.nnz * 4 / 1e9:.2f} GB of remap slots streamed per step)",
                        "parallelism": "replicas" if world > 1 else "single"},
             "all_mode_ms": step_ms, "per_mode_ms": per_mode_ms, "bytes_per_step": step_b,
             "frac_of_hbm_peak": value / world / peak, "bf16": bf16, "preprocess_ms": create_s * 1e3,
