@@ -100,7 +100,7 @@ typedef struct flycoo_tensor *flycoo_handle;
 /* preprocessing of Section V-J).  For every mode n it computes the layout   */
 /* L_n: nonzeros ordered by their super-shard ids (ss_n, ss_{n-1}, ...,      */
 /* ss_{n+1}, input position) with ss_w = c_w div m[w], cut into super-shards */
-/* and shards, and inside each shard every run of `tile` (512) positions     */
+/* and shards, and inside each shard every run of `tile` (2048) positions    */
 /* from the shard start stably re-ordered by c_n; each nonzero's slot in     */
 /* L_{(n+1) mod N}; and the Algorithm 3 schedules.  The tensor is then       */
 /* stored in layout L_0.                                                     */
@@ -112,8 +112,9 @@ typedef struct flycoo_tensor *flycoo_handle;
 /*  d_vals  nnz float32 values.  Copied.                                     */
 /*  params  NULL or partition parameters (zeros = defaults).                 */
 /*  out     receives the handle.                                             */
-/* Errors: INVALID_ARG (also m[n] > 128), INDEX_RANGE (any coordinate >= its */
-/* I_w), OOM, CUDA.  Waits for `stream`.                                     */
+/* Errors: INVALID_ARG (also m[n] > 128 or an unknown schedule),             */
+/* INDEX_RANGE (any coordinate >= its I_w), UNSUPPORTED (N outside 3..5,     */
+/* nnz >= 2^32 - 1), OOM, CUDA.  Waits for `stream`.                         */
 /* ------------------------------------------------------------------------ */
 flycoo_status flycoo_create(int N, const uint64_t *h_dims, uint64_t nnz, const uint32_t *d_idx,
                             const float *d_vals, const flycoo_params *params,
@@ -139,7 +140,8 @@ void flycoo_destroy(flycoo_handle h);
 /*  next_mode  -1: no remap.  (mode + 1) mod N: store every nonzero at its   */
 /*             slot of L_next during the pass (Algorithm 2, the Store of the  */
 /*             remap step); the tensor is then in layout L_next.             */
-/* Errors: INVALID_ARG, LAYOUT (tensor not in L_mode), UNSUPPORTED, CUDA.    */
+/* Errors: INVALID_ARG, LAYOUT (tensor not in L_mode, or a remapping pass   */
+/* on this handle gave up, see flycoo_sync), UNSUPPORTED, CUDA.              */
 /* ------------------------------------------------------------------------ */
 flycoo_status flycoo_spmttkrp(flycoo_handle h, int mode, const void *const *h_factors,
                               flycoo_dtype fdt, int R, float *d_out, int next_mode,
@@ -148,10 +150,10 @@ flycoo_status flycoo_spmttkrp(flycoo_handle h, int mode, const void *const *h_fa
 /* ------------------------------------------------------------------------ */
 /* flycoo_spmttkrp_static_scratch -- the paper has no counterpart; this is a  */
 /* library convenience.  Same computation, arguments, errors and results as   */
-/* flycoo_spmttkrp, but the call allocates nothing: the partial rows of the   */
-/* rows that straddle shard boundaries go to a fixed device array inside the  */
-/* library (8 MiB per GPU, held by every GPU that loads the library until the */
-/* process exits) instead of the scratch buffer flycoo_create allocated.      */
+/* flycoo_spmttkrp, but the call allocates nothing: the row blocks of the    */
+/* super-shards that span several shards go to a fixed device array inside   */
+/* the library (8 MiB per GPU, held by every GPU that loads the library until */
+/* the process exits) instead of the scratch buffer flycoo_create allocated.  */
 /* It is meant for callers that must not allocate device memory at the point  */
 /* of the call, for example code running while another allocator owns the    */
 /* GPU's free memory, or code that must not enter cudaMalloc on a time-bound  */
