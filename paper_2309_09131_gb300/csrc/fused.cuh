@@ -346,8 +346,11 @@ __global__ void __launch_bounds__(256, kBlocksPerSM) fused_mttkrp_remap_kernel(c
         // (odd, so the groups of a warp read different shared-memory banks).  A
         // run of one row that lies inside the slice is added by this group
         // alone; a run that crosses a slice edge is summed in step 3.
-        const u32 chunk = ((tlen + G - 1) / G) | 1u;
-        const u32 geff = (tlen + chunk - 1) / chunk;
+        // (a full tile, the common case, takes the compile-time values)
+        constexpr u32 kChunkFull = ((u32)(CAP + G - 1) / G) | 1u;
+        constexpr u32 kGeffFull = ((u32)CAP + kChunkFull - 1) / kChunkFull;
+        const u32 chunk = (tlen == (u32)CAP) ? kChunkFull : (((tlen + G - 1) / G) | 1u);
+        const u32 geff = (tlen == (u32)CAP) ? kGeffFull : (tlen + chunk - 1) / chunk;
         const u32 *sw = reinterpret_cast<const u32 *>(sb); // word 0 of a stored nonzero is its row index
         const u32 lo = min((u32)grp * chunk, tlen);
         const u32 hi = min(lo + chunk, tlen);
