@@ -4,40 +4,42 @@
 //
 // Layout.  The tensor is in layout L_n: nonzeros ordered by super-shard id
 // ss_n = c_n div m_n, cut into shards of at most g consecutive nonzeros
-// (Section III-A).  Inside a super-shard the nonzeros are ordered by the
-// other modes' super-shard ids, so the remap to L_{n+1} is a stable scatter
-// into the k_{n+1} super-shards of the next mode (a few hundred write streams
-// rather than one per output row).
+// (Section III-A).  Inside a super-shard the nonzeros are ordered by the other
+// modes' super-shard ids, so the remap to L_{n+1} is a stable scatter into the
+// k_{n+1} super-shards of the next mode (a few hundred write streams rather
+// than one per output row).  Inside a shard every sort unit of kSortTile
+// positions is stored sorted by c_n, so a row's nonzeros are contiguous in it.
 //
-// Work decomposition.  Thread block b walks the shards that Algorithm 3 put in
-// bin b.  A shard's super-shard owns m_n output rows, which the block
-// accumulates in shared memory (the paper keeps them in cache, Eq. 3).  One
-// elected thread streams the shard's layout tiles (512 nonzeros) into a
-// double-buffered shared-memory stage with 1-D TMA bulk copies (cp.async.bulk
-// on an mbarrier), one tile ahead.  For each tile:
+// Work decomposition.  Thread block b walks the stage tiles of the shards that
+// Algorithm 3 put in bin b (1024 positions when three such blocks fit on an SM,
+// else 512; a tile never crosses a sort unit).  A shard's super-shard owns m_n
+// output rows, which the block accumulates in shared memory (the paper keeps
+// them in cache, Eq. 3).  One thread streams the tiles with 1-D TMA bulk copies
+// into a two-stage shared buffer on mbarriers, two tiles ahead, and publishes
+// each tile's 16-byte descriptor with it.  For each tile:
 //
-//  1. remap: every thread stores a few of the tile's nonzeros at their slots
-//     of L_{n+1} (Algorithm 2, the Store of the remap step), the whole tile in
-//     one burst so neighbouring slots reach L2 together;
-//  2. compute: the tile is stored sorted by row (K1 sorts every layout tile),
-//     and each group of L lanes owns a contiguous slice of it; its lanes
-//     split the rank dimension (16 bytes of a factor row per
-//     lane, one coalesced vector load per lane and row).  Per nonzero it
-//     gathers the N-1 input factor rows and adds val * Hadamard product (FP32)
-//     to a running row sum in registers; a row that ends inside the slice is
-//     added to its shared-memory accumulator;
-//  3. combine: after a block barrier, the rows that touch a slice boundary
-//     are summed over the slices in slice order and added to the accumulator.
+//  1. remap: every thread stores a few of the tile's nonzeros at their slots of
+//     L_{n+1} (the Store of Algorithm 2's remap step), in one burst;
+//  2. compute: each group of L lanes takes a fixed slice of the tile; its lanes
+//     split the rank dimension (16 bytes of a factor row per lane).  Per
+//     nonzero it gathers the N-1 input factor rows and adds val * Hadamard
+//     product (FP32) to a running row sum in registers.  A run of one row that
+//     lies inside the slice is added to its shared-memory accumulator by the
+//     group alone;
+//  3. combine: a run that crosses a slice edge is summed after the block
+//     barrier, in slice order, by the group where it starts; when no run
+//     crosses an edge this step and its barrier are skipped.
 //
 // At the end of a shard the accumulator rows go straight to the output when
-// the super-shard has no other shard, else to the shard's row block; K4 then
-// sums the blocks of a super-shard in shard order.  Every accumulator row is
-// updated by one thread group at a time, in an order fixed by the layout and
-// the launch shape, so results are bitwise reproducible; no atomics touch the
-// data.  Rows without nonzeros come out as zeros.
+// the super-shard has no other shard, else to the shard's row block, and the
+// accumulator is zeroed; K4 then sums the blocks of a super-shard in shard
+// order.  Every accumulator row is updated by one thread group at a time, in an
+// order fixed by the layout and the launch shape, so results are bitwise
+// reproducible; no atomics touch the data.  Rows without nonzeros come out as
+// zeros.
 //
-// Every wait on an mbarrier is bounded; a wait that gives up sets the error
-// word and the whole block returns.
+// Every wait on an mbarrier is bounded; a block whose wait gives up sets the
+// error word, lets its copies in flight land (bounded) and returns.
 #pragma once
 
 #include "internal.cuh"
@@ -218,12 +220,6 @@ __device__ __forceinline__ void add_vec(float *acc, const float *src) {
     load_vec<VEC>(src, x);
 #pragma unroll
     for (int v = 0; v < VEC; ++v) acc[v] += x[v];
-}
-
-template <int VEC>
-__device__ __forceinline__ void store_zero(float *dst) {
-#pragma unroll
-    for (int q = 0; q < VEC / 4; ++q) reinterpret_cast<float4 *>(dst)[q] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
 // A tile descriptor: four words start, len | flags << 16, super-shard, shard.

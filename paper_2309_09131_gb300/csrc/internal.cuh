@@ -163,7 +163,6 @@ constexpr u32 kSortTile = FLYCOO_SORT_TILE;
 // inside sort units, and the schedule is described for both sizes
 constexpr u32 kStageTile[2] = {512u, 1024u};
 static_assert(kSortTile % 1024u == 0, "a sort unit is a whole number of stage tiles");
-constexpr u32 kInvalidRow = 0xffffffffu;
 // iteration limit of every device-side wait (mbarrier polls); ~0.1-1 s
 constexpr u32 kSpinLimit = 1u << 24;
 
