@@ -65,7 +65,8 @@ struct FusedCfg {
     static constexpr size_t stage_bytes(size_t cap) { return cap * EB + (cap + 8) * 4; }
     static constexpr size_t ACC = (size_t)M * R * 4;
     static constexpr size_t SUMBUF = (size_t)G * R * 4 + (((size_t)G * 4 + 15) & ~(size_t)15);
-    static constexpr size_t smem_bytes(size_t cap) { return 2 * stage_bytes(cap) + ACC + SUMBUF + 64; }
+    // + 96 bytes: two mbarriers and four 16-byte descriptor slots
+    static constexpr size_t smem_bytes(size_t cap) { return 2 * stage_bytes(cap) + ACC + SUMBUF + 96; }
     // the larger stage tile when kBlocksPerSM blocks of it fit in an SM's 228 KB
     // (1 KB of each block is reserved by the system)
     static constexpr int TZ = (kBlocksPerSM * (smem_bytes(kStageTile[1]) + 1024) <= 228 * 1024) ? 1 : 0;
@@ -156,6 +157,17 @@ __device__ __forceinline__ uint4 ld_factor(const uint4 *p, uint64_t policy) {
 #endif
 }
 
+// 16-byte cp.async (global -> shared) for thread 0's look-ahead descriptors:
+// the copy lands while the tile is computed; the thread waits for its own group
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int Pending>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(Pending) : "memory");
+}
+
 // bounded wait (at most `limit` polls); true on success
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, u32 parity, u32 limit = kSpinLimit) {
     for (u32 i = 0; i < limit; ++i)
@@ -241,8 +253,8 @@ __global__ void __launch_bounds__(256, kBlocksPerSM) fused_mttkrp_remap_kernel(c
     float *hacc = acc + M * R;                                               // [G][R] head partials
     u32 *pass = reinterpret_cast<u32 *>(hacc + G * R);                       // [G]
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw + 2 * C::STAGE + C::ACC + C::SUMBUF);
-    // sdesc[0..1]: descriptor of the tile in each stage; sdesc[2]: thread 0's
-    // copy of the descriptor of the tile two ahead
+    // sdesc[0..1]: descriptor of the tile in each stage; sdesc[2 + (t & 1)]:
+    // thread 0's look-ahead copy of the descriptor of tile t
     uint4 *sdesc = reinterpret_cast<uint4 *>(bar + 2);
 
     const int tid = threadIdx.x;
@@ -295,7 +307,8 @@ __global__ void __launch_bounds__(256, kBlocksPerSM) fused_mttkrp_remap_kernel(c
     if (tid == 0) {
         if (ntile > 0) issue(0, tiles[t_begin]);
         if (ntile > 1) issue(1, tiles[t_begin + 1]);
-        if (ntile > 2) sdesc[2] = tiles[t_begin + 2];
+        if (ntile > 2) cp_async16(&sdesc[2], tiles + t_begin + 2);
+        cp_async_commit();
     }
 
     for (u32 q = 0; q < ntile; ++q) {
@@ -306,6 +319,10 @@ __global__ void __launch_bounds__(256, kBlocksPerSM) fused_mttkrp_remap_kernel(c
         // the arrive that the wait acquires); a tile that gave up uses length 1 and
         // touches no global memory, so every index below stays inside the stage
         const uint4 d = sdesc[st];
+        if (tid == 0) { // the descriptor of tile q + 3, needed when tile q + 1 ends
+            if (q + 3 < ntile) cp_async16(&sdesc[2 + ((q + 3) & 1)], tiles + t_begin + q + 3);
+            cp_async_commit();
+        }
         const u32 tstart = d.x;
         const u32 tlen = timed_out ? 1u : min(d.y & 0xffffu, (u32)CAP);
         const u32 flags = d.y >> 16;
@@ -475,13 +492,14 @@ __global__ void __launch_bounds__(256, kBlocksPerSM) fused_mttkrp_remap_kernel(c
                 // released (always with the full bound, whatever a.wait_limit is)
                 mbar_wait_bounded(&bar[st], (q >> 1) & 1u);
                 if (q + 1 < ntile) mbar_wait_bounded(&bar[st ^ 1], ((q + 1) >> 1) & 1u);
+                cp_async_wait<0>();
             }
             return;
         }
         // every thread is past its reads of this stage: load the tile after next into it
         if (tid == 0 && q + 2 < ntile) {
-            issue(st, sdesc[2]);
-            if (q + 3 < ntile) sdesc[2] = tiles[t_begin + q + 3];
+            cp_async_wait<1>(); // every group but the one committed at this tile's start
+            issue(st, sdesc[2 + ((q + 2) & 1)]);
         }
 
         // 3. rows longer than a chunk: the group where such a row starts adds the
@@ -514,6 +532,7 @@ __global__ void __launch_bounds__(256, kBlocksPerSM) fused_mttkrp_remap_kernel(c
             __syncthreads();
         }
     }
+    if (tid == 0) cp_async_wait<0>(); // no look-ahead copy outlives the block
     if constexpr (CPOPT) {
         // half the sum of squared residuals of this block, reduced in a fixed order
         if (a.loss_part) {
