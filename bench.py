@@ -483,7 +483,10 @@ def main(argv=None):
                        "parallelism": "replicas" if world > 1 else "single"},
             "all_mode_ms": step_ms, "per_mode_ms": per_mode_ms, "bytes_per_step": step_b,
             "frac_of_hbm_peak": value / world / peak, "bf16": bf16, "preprocess_ms": create_s * 1e3,
-            "generate_s": gen_s, "cp_als": als, "cpopt": cpopt, **extra, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "generate_s": gen_s, "cp_als": als, "cpopt": cpopt, **extra,
+            "memory": {"device_bytes": info["device_bytes"], "tensor_bytes": wl.nnz * elem_bytes,
+                       "device_over_tensor": info["device_bytes"] / max(1, wl.nnz * elem_bytes)},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches_per_step * args.steps, "clocks": clk,
         }
         print(json.dumps(line), flush=True)

@@ -108,6 +108,27 @@ class FlycooTensor:
                 break
         return lam, fits
 
+    def cp_als_state(self, factors: Sequence[torch.Tensor], lam: Optional[torch.Tensor], fits: List[float]) -> dict:
+        """Everything needed to resume CP-ALS: the factors, lambda, the fits so
+        far and the layout the tensor is in (a handle rebuilt from the same COO
+        input has the same layouts, so resuming is bitwise identical)."""
+        return {"factors": [f.detach().cpu().clone() for f in factors],
+                "lambda": None if lam is None else lam.detach().cpu().clone(),
+                "fits": list(fits), "iteration": len(fits), "layout_mode": self.layout_mode,
+                "dims": list(self.dims), "nnz": self.nnz}
+
+    @staticmethod
+    def save_cp_als_state(path: str, state: dict) -> None:
+        torch.save(state, path)
+
+    @staticmethod
+    def load_cp_als_state(path: str, device="cuda"):
+        """Returns ``(factors on device, lambda on device or None, fits)``."""
+        state = torch.load(path, map_location="cpu")
+        facs = [f.to(device).contiguous() for f in state["factors"]]
+        lam = None if state["lambda"] is None else state["lambda"].to(device)
+        return facs, lam, list(state["fits"])
+
     def remap(self, next_mode: int, stream=None) -> None:
         nat.flycoo_remap(self.h, next_mode, stream)
 
