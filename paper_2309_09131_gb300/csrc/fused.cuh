@@ -48,9 +48,20 @@
 
 namespace flycoo {
 
+// 16-byte loads of one factor row per lane for FP32 factors: a lane takes
+// FLYCOO_FP32_CHUNKS chunks of 4 values, chunk c from the c-th part of the row,
+// so every load instruction of a warp still covers whole sectors.  One chunk is
+// the default: with two, a warp's load instruction touches twice as many rows
+// (lines), which costs more in L1 than the shared per-nonzero work saves.
+#ifndef FLYCOO_FP32_CHUNKS
+#define FLYCOO_FP32_CHUNKS 1
+#endif
+
 template <int N, int R, bool BF16>
 struct FusedCfg {
-    static constexpr int VEC = BF16 ? 8 : 4;        // factor values per 16-byte load
+    static constexpr int CV = BF16 ? 8 : 4;         // factor values per 16-byte load
+    static constexpr int CPL = (BF16 || N >= 5) ? 1 : FLYCOO_FP32_CHUNKS; // 16-byte loads per row per lane
+    static constexpr int VEC = CPL * CV;            // factor values per lane
     static constexpr int L = R / VEC;               // lanes per group
     static constexpr int GPW = 32 / L;              // groups per warp
     static constexpr int WARPS = 8;
@@ -73,7 +84,7 @@ struct FusedCfg {
     static constexpr int CAP = (int)kStageTile[TZ];
     static constexpr size_t STAGE = stage_bytes(CAP);
     static constexpr size_t SMEM = smem_bytes(CAP);
-    static_assert(R % VEC == 0 && L >= 1 && L <= 32 && 32 % L == 0, "rank not supported");
+    static_assert(R % VEC == 0 && L >= 1 && L <= 32 && 32 % L == 0 && (R / CV) % CPL == 0, "rank not supported");
     static_assert(STAGE % 16 == 0 && SUMBUF % 16 == 0 && ACC % 16 == 0, "shared-memory alignment");
 };
 
@@ -241,13 +252,20 @@ template <int N, int R, bool BF16, bool CPOPT>
 __global__ void __launch_bounds__(256, kBlocksPerSM) fused_mttkrp_remap_kernel(const FusedArgs a) {
     using C = FusedCfg<N, R, BF16>;
     static_assert(!(CPOPT && BF16), "the CP-OPT gradient pass takes FP32 factors");
-    constexpr int VEC = C::VEC;
-    constexpr int RV = R / VEC; // 16-byte chunks per factor row
+    constexpr int VEC = C::VEC;     // factor values per lane
+    constexpr int CV = C::CV;       // values per 16-byte load
+    constexpr int CPL = C::CPL;     // 16-byte loads per row per lane
+    constexpr int RV = R / CV;      // 16-byte chunks per factor row
+    constexpr int RC = RV / CPL;    // 16-byte chunks per part of a row (lane k loads chunk k of each part)
     constexpr int CAP = C::CAP;
     constexpr int G = C::G;
     constexpr int M = C::M;
     constexpr int NF = CPOPT ? N : N - 1;            // factor rows gathered per nonzero
-    constexpr int U = (N == 3 && !CPOPT) ? FLYCOO_UNROLL3 : (N >= 5 ? 1 : 2); // nonzeros per group per step
+    // nonzeros per group per step: the gathered rows of a step take at most 32
+    // registers per lane (U * NF * CPL 16-byte loads)
+    constexpr int U = (N >= 5 || 8 / (NF * CPL) < 1)
+                          ? 1
+                          : ((8 / (NF * CPL)) > FLYCOO_UNROLL3 ? FLYCOO_UNROLL3 : 8 / (NF * CPL));
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float *acc = reinterpret_cast<float *>(smem_raw + 2 * C::STAGE);          // [M][R]
     float *hacc = acc + M * R;                                               // [G][R] head partials
@@ -271,7 +289,16 @@ __global__ void __launch_bounds__(256, kBlocksPerSM) fused_mttkrp_remap_kernel(c
     // CP-OPT: the output mode's own factor, for the model value at each nonzero
     const uint4 *Yo = CPOPT ? static_cast<const uint4 *>(a.Yout) + k : nullptr;
     double loss = 0.0;
-    float *my_hacc = hacc + grp * R + k * VEC;
+    float *my_hacc = hacc + grp * R;
+    // this lane's values of a row: part c holds columns c*(R/CPL) + k*CV .. + CV-1
+    auto lane_store = [&](float *row, const float *v) {
+#pragma unroll
+        for (int c = 0; c < CPL; ++c) store_vec<CV>(row + c * (R / CPL) + k * CV, v + c * CV);
+    };
+    auto lane_add = [&](float *v, const float *row) {
+#pragma unroll
+        for (int c = 0; c < CPL; ++c) add_vec<CV>(v + c * CV, row + c * (R / CPL) + k * CV);
+    };
     const uint64_t pol_stream = l2_policy_evict_first();
     const uint64_t pol_factor = l2_policy_evict_last();
     const uint4 *__restrict__ tiles = a.tiles[C::TZ];
@@ -386,7 +413,7 @@ __global__ void __launch_bounds__(256, kBlocksPerSM) fused_mttkrp_remap_kernel(c
         auto steps = [&](u32 j0, auto count) {
             constexpr int UU = decltype(count)::value;
             u32 w[UU][N + 1];
-            uint4 y[UU][NF];
+            uint4 y[UU][NF][CPL];
 #pragma unroll
             for (int u = 0; u < UU; ++u) {
                 const u32 p = min(lo + j0 + u, last);
@@ -402,19 +429,26 @@ __global__ void __launch_bounds__(256, kBlocksPerSM) fused_mttkrp_remap_kernel(c
 #pragma unroll
             for (int u = 0; u < UU; ++u) {
 #pragma unroll
-                for (int t = 0; t < N - 1; ++t) y[u][t] = ld_factor(Yp[t] + (size_t)w[u][t + 1] * RV, pol_factor);
-                if constexpr (CPOPT) y[u][N - 1] = ld_factor(Yo + (size_t)w[u][0] * RV, pol_factor);
+                for (int t = 0; t < N - 1; ++t)
+#pragma unroll
+                    for (int c = 0; c < CPL; ++c)
+                        y[u][t][c] = ld_factor(Yp[t] + (size_t)w[u][t + 1] * RV + c * RC, pol_factor);
+                if constexpr (CPOPT)
+#pragma unroll
+                    for (int c = 0; c < CPL; ++c) y[u][N - 1][c] = ld_factor(Yo + (size_t)w[u][0] * RV + c * RC, pol_factor);
             }
 #pragma unroll
             for (int u = 0; u < UU; ++u) {
                 const bool valid = lo + j0 + u < hi;
                 const u32 row = min(w[u][0] - row_base, (u32)M - 1u);
                 float prod[VEC];
-                widen<BF16>(y[u][0], prod);
+#pragma unroll
+                for (int c = 0; c < CPL; ++c) widen<BF16>(y[u][0][c], prod + c * CV);
 #pragma unroll
                 for (int t = 1; t < N - 1; ++t) {
                     float f[VEC];
-                    widen<BF16>(y[u][t], f);
+#pragma unroll
+                    for (int c = 0; c < CPL; ++c) widen<BF16>(y[u][t][c], f + c * CV);
 #pragma unroll
                     for (int v = 0; v < VEC; ++v) prod[v] *= f[v];
                 }
@@ -423,7 +457,8 @@ __global__ void __launch_bounds__(256, kBlocksPerSM) fused_mttkrp_remap_kernel(c
                 if constexpr (CPOPT) {
                     // model value m = <Y_n[c_n], prod>: lane partials summed over the group
                     float yo[VEC];
-                    widen<false>(y[u][N - 1], yo);
+#pragma unroll
+                    for (int c = 0; c < CPL; ++c) widen<false>(y[u][N - 1][c], yo + c * CV);
                     float mpart = 0.f;
 #pragma unroll
                     for (int v = 0; v < VEC; ++v) mpart = fmaf(yo[v], prod[v], mpart);
@@ -435,14 +470,14 @@ __global__ void __launch_bounds__(256, kBlocksPerSM) fused_mttkrp_remap_kernel(c
                 }
                 if (row != crow) {
                     if (first_run) {
-                        store_vec<VEC>(my_hacc, racc);
+                        lane_store(my_hacc, racc);
                         if (k == 0) pass[grp] = 0u;
                         first_run = false;
                     } else {
                         // a whole row of this tile: only this group holds it
-                        float *dst = acc + crow * R + k * VEC;
-                        add_vec<VEC>(racc, dst);
-                        store_vec<VEC>(dst, racc);
+                        float *dst = acc + crow * R;
+                        lane_add(racc, dst);
+                        lane_store(dst, racc);
                     }
                     crow = row;
 #pragma unroll
@@ -464,18 +499,18 @@ __global__ void __launch_bounds__(256, kBlocksPerSM) fused_mttkrp_remap_kernel(c
         if (!timed_out && lo < hi) {
             if (tail_shared) {
                 if (first_run) {
-                    store_vec<VEC>(my_hacc, racc);
+                    lane_store(my_hacc, racc);
                     if (k == 0) pass[grp] = 1u;
                 } else {
                     chain_start = true;
                 }
             } else if (first_run) {
-                store_vec<VEC>(my_hacc, racc);
+                lane_store(my_hacc, racc);
                 if (k == 0) pass[grp] = 0u;
             } else {
-                float *dst = acc + crow * R + k * VEC;
-                add_vec<VEC>(racc, dst);
-                store_vec<VEC>(dst, racc);
+                float *dst = acc + crow * R;
+                lane_add(racc, dst);
+                lane_store(dst, racc);
             }
         }
         // one barrier reports both: every lane of a warp that gave up counts (32 per
@@ -508,12 +543,12 @@ __global__ void __launch_bounds__(256, kBlocksPerSM) fused_mttkrp_remap_kernel(c
         if (nsync > 0) {
             if (chain_start) {
                 for (u32 g2 = grp + 1; g2 < geff; ++g2) {
-                    add_vec<VEC>(racc, hacc + g2 * R + k * VEC);
+                    lane_add(racc, hacc + g2 * R);
                     if (!pass[g2]) break;
                 }
-                float *dst = acc + crow * R + k * VEC;
-                add_vec<VEC>(racc, dst);
-                store_vec<VEC>(dst, racc);
+                float *dst = acc + crow * R;
+                lane_add(racc, dst);
+                lane_store(dst, racc);
             }
             // the next tile's slices may hold this row: their adds wait here
             __syncthreads();
