@@ -56,11 +56,16 @@ namespace flycoo {
 #ifndef FLYCOO_FP32_CHUNKS
 #define FLYCOO_FP32_CHUNKS 1
 #endif
+// the same for R = 64, where a row is two lines and two chunks per lane still
+// keep each warp load at four lines
+#ifndef FLYCOO_FP32_CHUNKS_R64
+#define FLYCOO_FP32_CHUNKS_R64 2
+#endif
 
 template <int N, int R, bool BF16>
 struct FusedCfg {
     static constexpr int CV = BF16 ? 8 : 4;         // factor values per 16-byte load
-    static constexpr int CPL = (BF16 || N >= 5) ? 1 : FLYCOO_FP32_CHUNKS; // 16-byte loads per row per lane
+    static constexpr int CPL = (BF16 || N >= 5) ? 1 : (R >= 64 ? FLYCOO_FP32_CHUNKS_R64 : FLYCOO_FP32_CHUNKS);
     static constexpr int VEC = CPL * CV;            // factor values per lane
     static constexpr int L = R / VEC;               // lanes per group
     static constexpr int GPW = 32 / L;              // groups per warp
