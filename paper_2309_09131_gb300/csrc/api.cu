@@ -1,6 +1,6 @@
 // api.cu -- the C ABI of include/flycoo.h: argument checks, the host-side
-// FLYCOO bookkeeping (Section III-A pointers, Algorithm 3 schedules,
-// boundary-row lists) and the dispatch of the kernels.
+// FLYCOO bookkeeping (Section III-A pointers, Algorithm 3 schedules, tile
+// descriptors, the K4 work list) and the dispatch of the kernels.
 #include "fused.cuh"
 
 #include <algorithm>
@@ -30,8 +30,7 @@ u64 Tensor::device_bytes() const {
     u64 b = elem[0].bytes + elem[1].bytes + partials.bytes + err.bytes + loss_part.bytes + als.bytes();
     for (int n = 0; n < N; ++n) {
         const ModeMeta &m = mode[n];
-        b += m.d_shard_ptr.bytes + m.d_shard_ss.bytes + m.d_ss_shard_ptr.bytes + m.d_bin_ptr.bytes +
-             m.d_items.bytes + m.d_k4.bytes + m.d_next.bytes + m.d_tiles[0].bytes + m.d_tiles[1].bytes +
+        b += m.d_ss_shard_ptr.bytes + m.d_k4.bytes + m.d_next.bytes + m.d_tiles[0].bytes + m.d_tiles[1].bytes +
              m.d_tile_bin_ptr[0].bytes + m.d_tile_bin_ptr[1].bytes;
     }
     return b;
@@ -191,11 +190,7 @@ flycoo_status partition_mode(Tensor &t, int n, const std::vector<u32> &ssp, cuda
     md.k4_items.clear();
     for (u64 j = 0; j < md.k; ++j)
         if (ss_shards[j] != 1) md.k4_items.push_back((u32)j);
-    FLY_TRY(upload(md.d_shard_ptr, md.shard_ptr, s));
-    FLY_TRY(upload(md.d_shard_ss, md.shard_ss, s));
     FLY_TRY(upload(md.d_ss_shard_ptr, md.ss_shard_ptr, s));
-    FLY_TRY(upload(md.d_bin_ptr, md.sh_bin_ptr, s));
-    FLY_TRY(upload(md.d_items, md.sh_items, s));
     FLY_TRY(upload(md.d_k4, md.k4_items, s));
     for (int z = 0; z < 2; ++z) {
         FLY_TRY(upload(md.d_tiles[z], md.tiles[z], s));
@@ -396,11 +391,6 @@ extern "C" flycoo_status flycoo_spmttkrp(flycoo_handle h, int mode, const void *
     a.next = next_mode >= 0 ? md.d_next.as<u32>() : nullptr;
     for (int q = 1; q < t.N; ++q) a.Y[q - 1] = h_factors[(mode + q) % t.N];
     a.out = d_out;
-    a.shard_ptr = md.d_shard_ptr.as<u32>();
-    a.shard_ss = md.d_shard_ss.as<u32>();
-    a.ss_shard_ptr = md.d_ss_shard_ptr.as<u32>();
-    a.bin_ptr = md.d_bin_ptr.as<u32>();
-    a.bin_items = md.d_items.as<u32>();
     for (int z = 0; z < 2; ++z) {
         a.tiles[z] = md.d_tiles[z].as<uint4>();
         a.tile_bin_ptr[z] = md.d_tile_bin_ptr[z].as<u32>();
@@ -409,7 +399,6 @@ extern "C" flycoo_status flycoo_spmttkrp(flycoo_handle h, int mode, const void *
     a.err = t.err.as<u32>();
     a.I_out = (u32)t.dims[mode];
     a.m = (u32)md.m;
-    a.S = (u32)md.S;
     a.bins = t.bins;
     a.wait_limit = t.wait_limit;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -466,11 +455,6 @@ flycoo_status flycoo::run_pass(Tensor &t, int mode, const void *const *F, flycoo
     a.next = md.d_next.as<u32>();
     for (int q = 1; q < t.N; ++q) a.Y[q - 1] = F[(mode + q) % t.N];
     a.out = d_out;
-    a.shard_ptr = md.d_shard_ptr.as<u32>();
-    a.shard_ss = md.d_shard_ss.as<u32>();
-    a.ss_shard_ptr = md.d_ss_shard_ptr.as<u32>();
-    a.bin_ptr = md.d_bin_ptr.as<u32>();
-    a.bin_items = md.d_items.as<u32>();
     for (int z = 0; z < 2; ++z) {
         a.tiles[z] = md.d_tiles[z].as<uint4>();
         a.tile_bin_ptr[z] = md.d_tile_bin_ptr[z].as<u32>();
@@ -481,7 +465,6 @@ flycoo_status flycoo::run_pass(Tensor &t, int mode, const void *const *F, flycoo
     a.loss_part = loss_part;
     a.I_out = (u32)t.dims[mode];
     a.m = (u32)md.m;
-    a.S = (u32)md.S;
     a.bins = t.bins;
     a.wait_limit = t.wait_limit;
     FLY_TRY(launch_fused(t.N, R, fdt, a, s));

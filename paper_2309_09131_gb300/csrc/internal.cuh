@@ -93,7 +93,7 @@ struct ModeMeta {
     // 4 the super-shard has no other shard
     // (one set per stage-tile size, kStageTile)
     std::vector<u32> tiles[2], tile_bin_ptr[2];
-    DevBuf d_shard_ptr, d_shard_ss, d_ss_shard_ptr, d_bin_ptr, d_items, d_k4, d_next;
+    DevBuf d_ss_shard_ptr, d_k4, d_next;
     DevBuf d_tiles[2], d_tile_bin_ptr[2];
 };
 
@@ -201,7 +201,7 @@ flycoo_status launch_export_layout(const Tensor &t, const void *elem, u32 *idx_o
                                    cudaStream_t s);
 
 // --------------------------------------------------------------------------
-// fused spMTTKRP + remap (K2) and boundary-row fixup (K4)
+// fused spMTTKRP + remap (K2) and the fixup of multi-shard super-shards (K4)
 // --------------------------------------------------------------------------
 struct FusedArgs {
     const void *elem_in;
@@ -209,10 +209,6 @@ struct FusedArgs {
     const u32 *next;           // nullptr: no remap
     const void *Y[FLYCOO_MAX_MODES - 1]; // factors of slots 1..N-1 of the current layout
     float *out;
-    const u32 *shard_ptr;      // S + 1
-    const u32 *shard_ss;       // S
-    const u32 *ss_shard_ptr;   // k + 1
-    const u32 *bin_ptr, *bin_items;
     const uint4 *tiles[2];     // tile descriptors, block-schedule order, per stage-tile size
     const u32 *tile_bin_ptr[2]; // bins + 1, per stage-tile size
     float *partials;           // row block of shard s at s * m * R
@@ -221,8 +217,7 @@ struct FusedArgs {
     double *loss_part;         // CP-OPT pass: per-block half sum of squared residuals (nullable)
     u32 I_out;
     u32 m;                     // super-shard width of the output mode
-    u32 S;
-    u32 bins;
+    u32 bins;                  // thread blocks (schedule bins)
     u32 wait_limit;            // polls of a tile's barrier before the pass gives up
 };
 

@@ -130,11 +130,6 @@ extern "C" flycoo_status flycoo_spmttkrp_static_scratch(flycoo_handle h, int mod
     a.next = next_mode >= 0 ? md.d_next.as<u32>() : nullptr;
     for (int q = 1; q < t.N; ++q) a.Y[q - 1] = h_factors[(mode + q) % t.N];
     a.out = d_out;
-    a.shard_ptr = md.d_shard_ptr.as<u32>();
-    a.shard_ss = md.d_shard_ss.as<u32>();
-    a.ss_shard_ptr = md.d_ss_shard_ptr.as<u32>();
-    a.bin_ptr = md.d_bin_ptr.as<u32>();
-    a.bin_items = md.d_items.as<u32>();
     for (int z = 0; z < 2; ++z) {
         a.tiles[z] = md.d_tiles[z].as<uint4>();
         a.tile_bin_ptr[z] = md.d_tile_bin_ptr[z].as<u32>();
@@ -143,7 +138,6 @@ extern "C" flycoo_status flycoo_spmttkrp_static_scratch(flycoo_handle h, int mod
     a.err = t.err.as<u32>();
     a.I_out = (u32)t.dims[mode];
     a.m = (u32)md.m;
-    a.S = (u32)md.S;
     a.bins = t.bins;
     a.wait_limit = t.wait_limit;
     FLY_TRY(launch_fused(t.N, R, fdt, a, s));
