@@ -211,10 +211,11 @@ def _draw_mode(rng, law: tuple, I: int, size: int, hot_ids: Optional[np.ndarray]
 
 
 def _split_point(dims: Sequence[int]) -> int:
-    """Largest k such that prod(dims[:k]) fits in 62 bits (at least 1)."""
+    """Largest k such that every key of the first k modes fits in an unsigned
+    64-bit integer, i.e. prod(dims[:k]) <= 2^64 (at least 1)."""
     p = 1
     for k, d in enumerate(dims):
-        if p * d >= (1 << 62):
+        if p * d > (1 << 64):
             return max(k, 1)
         p *= d
     return len(dims)
