@@ -61,7 +61,8 @@ typedef enum {
  *        consecutive nonzeros (the last one shorter).  Default: the largest
  *        power of two in [1024, 32768] that leaves about four shards per bin.
  *  bins  number of schedule bins of Algorithm 3, which is also the number of
- *        thread blocks of the fused kernel.  Default: 3 x the SM count.
+ *        thread blocks of the fused kernel; at most 2^20.  Default: 3 x the
+ *        SM count.
  *  schedule  FLYCOO_SCHEDULE_LPT (0, default): Algorithm 3 -- items sorted by
  *        size, each to the least-loaded bin; FLYCOO_SCHEDULE_BLOCK_CYCLIC (1):
  *        item i to bin i mod bins, in ascending order (the baseline the paper
@@ -112,7 +113,7 @@ typedef struct flycoo_tensor *flycoo_handle;
 /*  d_vals  nnz float32 values.  Copied.                                     */
 /*  params  NULL or partition parameters (zeros = defaults).                 */
 /*  out     receives the handle.                                             */
-/* Errors: INVALID_ARG (also m[n] > 128 or an unknown schedule),             */
+/* Errors: INVALID_ARG (also m[n] > 128, bins > 2^20, unknown schedule),    */
 /* INDEX_RANGE (any coordinate >= its I_w), UNSUPPORTED (N outside 3..5,     */
 /* nnz >= 2^32 - 1), OOM, CUDA.  Waits for `stream`.                         */
 /* ------------------------------------------------------------------------ */
@@ -293,6 +294,63 @@ flycoo_status flycoo_export_schedule(flycoo_handle h, int mode, int which, uint6
 /* position p of L_mode -- the remap permutation of mode `mode`.             */
 flycoo_status flycoo_export_next(flycoo_handle h, int mode, uint32_t *d_next,
                                  flycoo_stream_t stream);
+
+/* ------------------------------------------------------------------------ */
+/* Host-only planner: the partition and schedule step of flycoo_create for   */
+/* one mode, on its own.  It touches no device (it runs where no GPU is).    */
+/* ------------------------------------------------------------------------ */
+typedef struct flycoo_plan_s *flycoo_plan;
+
+/* From the super-shard pointers of one mode (Section III-A), cut every      */
+/* super-shard into shards of g nonzeros, schedule the super-shards by shard */
+/* count and the shards by nonzero count (Algorithm 3, or block-cyclic), and */
+/* write the shard schedule out as the fused kernel's tile descriptors.      */
+/* flycoo_create runs exactly this for every mode of a handle.               */
+/*  nnz       nonzeros, < 2^32 - 1.                                          */
+/*  k         super-shards k_n = ceil(I_n / m_n), in [1, 2^32 - 2].          */
+/*  h_ss_ptr  k + 1 host values: start of super-shard j in L_n, then nnz;    */
+/*            0 = h_ss_ptr[0] <= h_ss_ptr[1] <= ... <= h_ss_ptr[k] = nnz.     */
+/*            Copied.                                                        */
+/*  g         shard size; 0 = flycoo_create's default for nnz and bins.     */
+/*  bins      schedule bins, in [1, 2^20].                                   */
+/*  schedule  FLYCOO_SCHEDULE_LPT or FLYCOO_SCHEDULE_BLOCK_CYCLIC.           */
+/*  out       receives the plan; the caller frees it with flycoo_plan_destroy*/
+/* Errors: INVALID_ARG (NULL pointers, k, bins, schedule or g out of range,  */
+/* pointers that do not split [0, nnz]), UNSUPPORTED (nnz >= 2^32 - 1), OOM  */
+/* (host allocation).                                                        */
+flycoo_status flycoo_plan_create(uint64_t nnz, uint64_t k, const uint64_t *h_ss_ptr, uint64_t g,
+                                 uint32_t bins, uint32_t schedule, flycoo_plan *out);
+
+/* Arrays of a plan.  S = shards, T_z = stage tiles of size 512 (z = 0) or   */
+/* 1024 (z = 1).  Schedules are CSR lists: bin b holds                       */
+/* items[bin_ptr[b] .. bin_ptr[b+1]) in assignment order.  A tile descriptor */
+/* is four values (start, len | flags << 16, super-shard, shard), flags 1 =  */
+/* first tile of its shard, 2 = last, 4 = the only shard of its super-shard; */
+/* descriptors run bin by bin in the order of the shard schedule.           */
+typedef enum {
+    FLYCOO_PLAN_G = 0,              /* 1: the shard size used                 */
+    FLYCOO_PLAN_SHARD_PTR = 1,      /* S + 1: start of each shard, then nnz   */
+    FLYCOO_PLAN_SHARD_SS = 2,       /* S: super-shard of each shard           */
+    FLYCOO_PLAN_SS_SHARD_PTR = 3,   /* k + 1: first shard of each super-shard */
+    FLYCOO_PLAN_SS_BIN_PTR = 4,     /* bins + 1: super-shard schedule         */
+    FLYCOO_PLAN_SS_ITEMS = 5,       /* k                                      */
+    FLYCOO_PLAN_SHARD_BIN_PTR = 6,  /* bins + 1: shard (thread-block) schedule*/
+    FLYCOO_PLAN_SHARD_ITEMS = 7,    /* S                                      */
+    FLYCOO_PLAN_K4_ITEMS = 8,       /* super-shards without exactly one shard */
+    FLYCOO_PLAN_TILE_BIN_PTR_512 = 9,   /* bins + 1, in descriptors           */
+    FLYCOO_PLAN_TILES_512 = 10,         /* 4 x T_0                            */
+    FLYCOO_PLAN_TILE_BIN_PTR_1024 = 11, /* bins + 1                           */
+    FLYCOO_PLAN_TILES_1024 = 12         /* 4 x T_1                            */
+} flycoo_plan_array;
+
+/* Copy array `which` into h_out, widened to uint64.  *count is in: the     */
+/* capacity of h_out; out: the array's length.  h_out NULL only reports the  */
+/* length.  Errors: INVALID_ARG (NULL plan or count, unknown array, capacity */
+/* too small -- *count then holds the length needed).                       */
+flycoo_status flycoo_plan_get(flycoo_plan p, int which, uint64_t *h_out, uint64_t *count);
+
+/* Free a plan (NULL is ignored). */
+void flycoo_plan_destroy(flycoo_plan p);
 
 /* ------------------------------------------------------------------------ */
 /* Kernel timing of the fused spMTTKRP + remap kernel.  While enabled, each  */

@@ -21,6 +21,9 @@ from ._native import (  # noqa: F401
     flycoo_get_info,
     flycoo_last_error,
     flycoo_mttkrp_adjoint,
+    flycoo_plan_create,
+    flycoo_plan_destroy,
+    flycoo_plan_get,
     flycoo_remap,
     flycoo_spmttkrp,
     flycoo_spmttkrp_static_scratch,

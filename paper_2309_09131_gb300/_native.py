@@ -78,12 +78,16 @@ def lib():
             "flycoo_last_error": [],
             "flycoo_debug_set_wait_limit": [P, ctypes.c_int64],
             "flycoo_debug_fail_alloc_after": [ctypes.c_int64],
+            "flycoo_plan_create": [U64, U64, P, U64, U32, U32, P],
+            "flycoo_plan_get": [P, I, P, P],
+            "flycoo_plan_destroy": [P],
         }
         for name, args in sigs.items():
             fn = getattr(L, name)
             fn.argtypes = args
             fn.restype = ctypes.c_int
         L.flycoo_destroy.restype = None
+        L.flycoo_plan_destroy.restype = None
         L.flycoo_last_error.restype = ctypes.c_char_p
         _lib = L
     return _lib
@@ -338,6 +342,44 @@ def flycoo_timing_read(h):
     n = ctypes.c_uint64()
     _check(lib().flycoo_timing_read(h, ctypes.byref(ms), ctypes.byref(n)))
     return ms.value, n.value
+
+
+PLAN_G = 0
+PLAN_SHARD_PTR = 1
+PLAN_SHARD_SS = 2
+PLAN_SS_SHARD_PTR = 3
+PLAN_SS_BIN_PTR = 4
+PLAN_SS_ITEMS = 5
+PLAN_SHARD_BIN_PTR = 6
+PLAN_SHARD_ITEMS = 7
+PLAN_K4_ITEMS = 8
+PLAN_TILE_BIN_PTR_512 = 9
+PLAN_TILES_512 = 10
+PLAN_TILE_BIN_PTR_1024 = 11
+PLAN_TILES_1024 = 12
+
+
+def flycoo_plan_create(nnz: int, ss_ptr, g: int = 0, bins: int = 1, schedule: int = SCHEDULE_LPT):
+    """Host-only plan of one mode from its super-shard pointers (no device)."""
+    ss = np.ascontiguousarray(ss_ptr, dtype=np.uint64)
+    if ss.ndim != 1 or ss.size < 2:
+        raise ValueError("ss_ptr needs k + 1 >= 2 entries")
+    out = ctypes.c_void_p()
+    _check(lib().flycoo_plan_create(int(nnz), int(ss.size - 1), ss.ctypes.data, int(g), int(bins),
+                                    int(schedule), ctypes.byref(out)))
+    return out
+
+
+def flycoo_plan_get(plan, which: int) -> np.ndarray:
+    n = ctypes.c_uint64(0)
+    _check(lib().flycoo_plan_get(plan, int(which), None, ctypes.byref(n)))
+    buf = np.empty(n.value, dtype=np.uint64)
+    _check(lib().flycoo_plan_get(plan, int(which), buf.ctypes.data, ctypes.byref(n)))
+    return buf
+
+
+def flycoo_plan_destroy(plan) -> None:
+    lib().flycoo_plan_destroy(plan)
 
 
 def header_functions(header: Optional[str] = None) -> List[str]:

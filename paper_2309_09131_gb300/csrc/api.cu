@@ -8,8 +8,10 @@
 #include <cstdio>
 #include <functional>
 #include <memory>
+#include <new>
 #include <numeric>
 #include <queue>
+#include <stdexcept>
 
 namespace flycoo {
 
@@ -94,9 +96,21 @@ static flycoo_status upload(DevBuf &d, const std::vector<T> &h, cudaStream_t s) 
     return FLYCOO_OK;
 }
 
-// Section III-A pointers of one mode from its super-shard pointers, plus the
-// super-shard of every shard, both schedules and the K4 work list.
 long long g_alloc_fail_after = -1;
+
+// runs an entry point's body; a failed host allocation becomes FLYCOO_ERR_OOM
+// instead of an exception crossing the C ABI
+template <class F> static flycoo_status host_guarded(const char *who, F &&body) {
+    try {
+        return body();
+    } catch (const std::bad_alloc &) {
+        set_error("%s: a host allocation failed", who);
+        return FLYCOO_ERR_OOM;
+    } catch (const std::exception &e) {
+        set_error("%s: %s", who, e.what());
+        return FLYCOO_ERR_CUDA;
+    }
+}
 
 // a handle whose remapping pass gave up has an undefined layout
 flycoo_status check_usable(const Tensor &t, const char *who) {
@@ -128,49 +142,55 @@ flycoo_status check_error_word(Tensor &t, cudaStream_t s, const char *who) {
     return FLYCOO_OK;
 }
 
-flycoo_status partition_mode(Tensor &t, int n, const std::vector<u32> &ssp, cudaStream_t s) {
-    ModeMeta &md = t.mode[n];
-    const u64 I = t.dims[n];
-    md.I = I;
-    md.k = (I + md.m - 1) / md.m;
-    md.ss_ptr.assign(ssp.begin(), ssp.end());
+// about four shards per bin, a power of two in [1024, 32768]
+u64 default_shard_size(u64 nnz, u32 bins) {
+    u64 g = 32768;
+    while (g > 1024 && nnz / g < 4ull * bins) g >>= 1;
+    return g;
+}
+
+// Section III-A: super-shard j is cut into runs of g consecutive nonzeros
+// (shards); Algorithm 3 (or block-cyclic) schedules the super-shards by shard
+// count and the shards by nonzero count; the block schedule of the shards is
+// written out as tile descriptors for both stage-tile sizes.
+void plan_mode(ModePlan &md, u64 nnz, u64 g, u32 bins, u32 schedule) {
     md.shard_ptr.clear();
     md.shard_ss.clear();
     md.ss_shard_ptr.assign(md.k + 1, 0);
     std::vector<u64> ss_shards(md.k);
     for (u64 j = 0; j < md.k; ++j) {
         const u64 size = md.ss_ptr[j + 1] - md.ss_ptr[j];
-        ss_shards[j] = (size + t.g - 1) / t.g;
+        ss_shards[j] = (size + g - 1) / g;
         md.ss_shard_ptr[j] = (u32)md.shard_ptr.size();
-        for (u64 q = 0; q * t.g < size; ++q) {
-            md.shard_ptr.push_back((u32)(md.ss_ptr[j] + q * t.g));
+        for (u64 q = 0; q * g < size; ++q) {
+            md.shard_ptr.push_back((u32)(md.ss_ptr[j] + q * g));
             md.shard_ss.push_back((u32)j);
         }
     }
     md.S = md.shard_ptr.size();
     md.ss_shard_ptr[md.k] = (u32)md.S;
-    md.shard_ptr.push_back((u32)t.nnz);
+    md.shard_ptr.push_back((u32)nnz);
     std::vector<u64> shard_size(md.S);
     md.tile_ptr.clear();
     for (u64 q = 0; q < md.S; ++q) {
         shard_size[q] = md.shard_ptr[q + 1] - md.shard_ptr[q];
         for (u64 p = md.shard_ptr[q]; p < md.shard_ptr[q + 1]; p += kSortTile) md.tile_ptr.push_back((u32)p);
     }
-    md.tile_ptr.push_back((u32)t.nnz);
-    if (t.schedule == FLYCOO_SCHEDULE_BLOCK_CYCLIC) {
-        block_cyclic_schedule(ss_shards.size(), t.bins, md.ss_bin_ptr, md.ss_items);
-        block_cyclic_schedule(shard_size.size(), t.bins, md.sh_bin_ptr, md.sh_items);
+    md.tile_ptr.push_back((u32)nnz);
+    if (schedule == FLYCOO_SCHEDULE_BLOCK_CYCLIC) {
+        block_cyclic_schedule(ss_shards.size(), bins, md.ss_bin_ptr, md.ss_items);
+        block_cyclic_schedule(shard_size.size(), bins, md.sh_bin_ptr, md.sh_items);
     } else {
-        lpt_schedule(ss_shards, t.bins, md.ss_bin_ptr, md.ss_items);
-        lpt_schedule(shard_size, t.bins, md.sh_bin_ptr, md.sh_items);
+        lpt_schedule(ss_shards, bins, md.ss_bin_ptr, md.ss_items);
+        lpt_schedule(shard_size, bins, md.sh_bin_ptr, md.sh_items);
     }
     // tile descriptors of the block schedule, for both stage-tile sizes
     for (int z = 0; z < 2; ++z) {
         const u32 tile = kStageTile[z];
         std::vector<u32> &td = md.tiles[z];
         td.clear();
-        md.tile_bin_ptr[z].assign((size_t)t.bins + 1, 0);
-        for (u32 b = 0; b < t.bins; ++b) {
+        md.tile_bin_ptr[z].assign((size_t)bins + 1, 0);
+        for (u32 b = 0; b < bins; ++b) {
             md.tile_bin_ptr[z][b] = (u32)(td.size() / 4);
             for (u64 it = md.sh_bin_ptr[b]; it < md.sh_bin_ptr[b + 1]; ++it) {
                 const u32 sh = md.sh_items[it];
@@ -184,12 +204,21 @@ flycoo_status partition_mode(Tensor &t, int n, const std::vector<u32> &ssp, cuda
                 }
             }
         }
-        md.tile_bin_ptr[z][t.bins] = (u32)(td.size() / 4);
+        md.tile_bin_ptr[z][bins] = (u32)(td.size() / 4);
     }
     // K4 writes the rows of every super-shard that does not have exactly one shard
     md.k4_items.clear();
     for (u64 j = 0; j < md.k; ++j)
         if (ss_shards[j] != 1) md.k4_items.push_back((u32)j);
+}
+
+flycoo_status partition_mode(Tensor &t, int n, const std::vector<u32> &ssp, cudaStream_t s) {
+    ModeMeta &md = t.mode[n];
+    const u64 I = t.dims[n];
+    md.I = I;
+    md.k = (I + md.m - 1) / md.m;
+    md.ss_ptr.assign(ssp.begin(), ssp.end());
+    plan_mode(md, t.nnz, t.g, t.bins, t.schedule);
     FLY_TRY(upload(md.d_ss_shard_ptr, md.ss_shard_ptr, s));
     FLY_TRY(upload(md.d_k4, md.k4_items, s));
     for (int z = 0; z < 2; ++z) {
@@ -234,10 +263,9 @@ using namespace flycoo;
 // --------------------------------------------------------------------------
 extern "C" const char *flycoo_last_error(void) { return g_last_error.c_str(); }
 
-extern "C" flycoo_status flycoo_create(int N, const uint64_t *h_dims, uint64_t nnz, const uint32_t *d_idx,
-                                       const float *d_vals, const flycoo_params *params,
-                                       flycoo_stream_t stream, flycoo_handle *out) {
-    clear_error();
+static flycoo_status create_impl(int N, const uint64_t *h_dims, uint64_t nnz, const uint32_t *d_idx,
+                                 const float *d_vals, const flycoo_params *params, flycoo_stream_t stream,
+                                 flycoo_handle *out) {
     if (!out) {
         set_error("flycoo_create: out is NULL");
         return FLYCOO_ERR_INVALID_ARG;
@@ -272,6 +300,10 @@ extern "C" flycoo_status flycoo_create(int N, const uint64_t *h_dims, uint64_t n
     t->nnz = nnz;
     for (int w = 0; w < N; ++w) t->dims[w] = h_dims[w];
     t->bins = (params && params->bins) ? params->bins : (u32)(kBlocksPerSM * t->sm_count);
+    if (t->bins > kMaxBins) {
+        set_error("flycoo_create: bins = %u exceeds %u", t->bins, kMaxBins);
+        return FLYCOO_ERR_INVALID_ARG;
+    }
     t->wait_limit = kSpinLimit;
     t->schedule = params ? params->schedule : FLYCOO_SCHEDULE_LPT;
     if (t->schedule != FLYCOO_SCHEDULE_LPT && t->schedule != FLYCOO_SCHEDULE_BLOCK_CYCLIC) {
@@ -281,10 +313,7 @@ extern "C" flycoo_status flycoo_create(int N, const uint64_t *h_dims, uint64_t n
     if (params && params->g) {
         t->g = params->g;
     } else {
-        // about four shards per bin, a power of two in [1024, 32768]
-        u64 g = 32768;
-        while (g > 1024 && nnz / g < 4ull * t->bins) g >>= 1;
-        t->g = g;
+        t->g = default_shard_size(nnz, t->bins);
     }
     if (t->g > 0xffffffffull) {
         set_error("flycoo_create: g too large");
@@ -314,6 +343,14 @@ extern "C" flycoo_status flycoo_create(int N, const uint64_t *h_dims, uint64_t n
     return FLYCOO_OK;
 }
 
+extern "C" flycoo_status flycoo_create(int N, const uint64_t *h_dims, uint64_t nnz, const uint32_t *d_idx,
+                                       const float *d_vals, const flycoo_params *params,
+                                       flycoo_stream_t stream, flycoo_handle *out) {
+    clear_error();
+    return host_guarded("flycoo_create",
+                        [&] { return create_impl(N, h_dims, nnz, d_idx, d_vals, params, stream, out); });
+}
+
 extern "C" void flycoo_destroy(flycoo_handle h) {
     if (!h) return;
     DeviceGuard dg(h->device);
@@ -321,7 +358,14 @@ extern "C" void flycoo_destroy(flycoo_handle h) {
     delete h;
 }
 
+// two events of the pool for one timed launch; also reserves the pending
+// entry, so nothing is allocated once the launch is enqueued
 static flycoo_status next_event_pair(Tensor &t, cudaEvent_t *a, cudaEvent_t *b) {
+    FLY_TRY(host_guarded("flycoo timing", [&] {
+        t.ev_pool.reserve(t.ev_used + 2);
+        t.ev_pending.reserve(t.ev_pending.size() + 1);
+        return FLYCOO_OK;
+    }));
     while (t.ev_pool.size() < t.ev_used + 2) {
         cudaEvent_t e;
         FLY_TRY_CUDA(cudaEventCreate(&e));
@@ -525,7 +569,7 @@ extern "C" flycoo_status flycoo_mttkrp_adjoint(flycoo_handle h, int mode, const 
     FLY_TRY(check_usable(t, "flycoo_mttkrp_adjoint"));
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     // the factor list of every pass: Y_w, with the output mode's slot holding G
-    std::vector<const void *> F(t.N);
+    const void *F[FLYCOO_MAX_MODES] = {};
     for (int w = 0; w < t.N; ++w) F[w] = (w == mode) ? (const void *)d_gout : (const void *)h_factors[w];
     const int first = (mode + 1) % t.N;
     while (t.layout != first) {
@@ -537,7 +581,7 @@ extern "C" flycoo_status flycoo_mttkrp_adjoint(flycoo_handle h, int mode, const 
     for (int q = 1; q < t.N; ++q) {
         const int w = (mode + q) % t.N;
         if (h_gfactors[w]) {
-            FLY_TRY(run_pass(t, w, F.data(), FLYCOO_F32, R, h_gfactors[w], nullptr, nullptr, s));
+            FLY_TRY(run_pass(t, w, F, FLYCOO_F32, R, h_gfactors[w], nullptr, nullptr, s));
         } else {
             FLY_TRY(launch_remap_step(t, w, t.elem[t.cur].p, t.elem[1 - t.cur].p, s));
             t.cur = 1 - t.cur;
@@ -571,6 +615,11 @@ extern "C" flycoo_status flycoo_cpopt_grad(flycoo_handle h, const float *const *
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const void *const *F = reinterpret_cast<const void *const *>(h_factors);
     double *lp = t.loss_part.as<double>();
+    std::vector<double> part; // per-block loss partials, allocated before any work is enqueued
+    if (h_loss) FLY_TRY(host_guarded("flycoo_cpopt_grad", [&] {
+        part.assign(t.bins, 0.0);
+        return FLYCOO_OK;
+    }));
     if (t.nnz) FLY_TRY_CUDA(cudaMemsetAsync(lp, 0, (size_t)t.bins * sizeof(double), s));
     const int start = t.layout;
     for (int q = 0; q < t.N; ++q) {
@@ -578,7 +627,6 @@ extern "C" flycoo_status flycoo_cpopt_grad(flycoo_handle h, const float *const *
         FLY_TRY(run_pass(t, n, F, FLYCOO_F32, R, h_grads[n], F[n], q == 0 ? lp : nullptr, s));
     }
     if (h_loss) {
-        std::vector<double> part(t.bins, 0.0);
         if (t.nnz)
             FLY_TRY_CUDA(cudaMemcpyAsync(part.data(), lp, (size_t)t.bins * sizeof(double), cudaMemcpyDeviceToHost, s));
         FLY_TRY(check_error_word(t, s, "flycoo_cpopt_grad"));
@@ -762,3 +810,109 @@ extern "C" flycoo_status flycoo_debug_fail_alloc_after(int64_t n) {
     g_alloc_fail_after = n < 0 ? -1 : n;
     return FLYCOO_OK;
 }
+
+// --------------------------------------------------------------------------
+// host-only planner
+// --------------------------------------------------------------------------
+struct flycoo_plan_s : flycoo::ModePlan {
+    u64 g = 0;
+    u32 bins = 0;
+};
+
+static flycoo_status plan_create_impl(uint64_t nnz, uint64_t k, const uint64_t *h_ss_ptr, uint64_t g,
+                                      uint32_t bins, uint32_t schedule, flycoo_plan *out) {
+    if (!out) {
+        set_error("flycoo_plan_create: out is NULL");
+        return FLYCOO_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    if (nnz >= 0xffffffffull) {
+        set_error("flycoo_plan_create: nnz must be < 2^32 - 1");
+        return FLYCOO_ERR_UNSUPPORTED;
+    }
+    if (!h_ss_ptr || k == 0 || k >= 0xffffffffull) {
+        set_error("flycoo_plan_create: need 1 <= k < 2^32 - 1 and k + 1 super-shard pointers");
+        return FLYCOO_ERR_INVALID_ARG;
+    }
+    if (bins == 0 || bins > kMaxBins) {
+        set_error("flycoo_plan_create: bins = %u outside [1, %u]", bins, kMaxBins);
+        return FLYCOO_ERR_INVALID_ARG;
+    }
+    if (schedule != FLYCOO_SCHEDULE_LPT && schedule != FLYCOO_SCHEDULE_BLOCK_CYCLIC) {
+        set_error("flycoo_plan_create: unknown schedule %u", schedule);
+        return FLYCOO_ERR_INVALID_ARG;
+    }
+    if (g == 0) g = default_shard_size(nnz, bins);
+    if (g > 0xffffffffull) {
+        set_error("flycoo_plan_create: g too large");
+        return FLYCOO_ERR_INVALID_ARG;
+    }
+    if (h_ss_ptr[0] != 0 || h_ss_ptr[k] != nnz) {
+        set_error("flycoo_plan_create: super-shard pointers must run from 0 to nnz");
+        return FLYCOO_ERR_INVALID_ARG;
+    }
+    for (u64 j = 0; j < k; ++j)
+        if (h_ss_ptr[j] > h_ss_ptr[j + 1]) {
+            set_error("flycoo_plan_create: super-shard pointer %llu decreases", (unsigned long long)j);
+            return FLYCOO_ERR_INVALID_ARG;
+        }
+    auto p = std::make_unique<flycoo_plan_s>();
+    p->k = k;
+    p->ss_ptr.assign(h_ss_ptr, h_ss_ptr + k + 1);
+    p->g = g;
+    p->bins = bins;
+    plan_mode(*p, nnz, g, bins, schedule);
+    *out = p.release();
+    return FLYCOO_OK;
+}
+
+extern "C" flycoo_status flycoo_plan_create(uint64_t nnz, uint64_t k, const uint64_t *h_ss_ptr, uint64_t g,
+                                            uint32_t bins, uint32_t schedule, flycoo_plan *out) {
+    clear_error();
+    return host_guarded("flycoo_plan_create",
+                        [&] { return plan_create_impl(nnz, k, h_ss_ptr, g, bins, schedule, out); });
+}
+
+extern "C" flycoo_status flycoo_plan_get(flycoo_plan p, int which, uint64_t *h_out, uint64_t *count) {
+    clear_error();
+    if (!p || !count) {
+        set_error("flycoo_plan_get: plan or count is NULL");
+        return FLYCOO_ERR_INVALID_ARG;
+    }
+    const u64 g1[1] = {p->g};
+    const u64 *wide = nullptr;
+    const std::vector<u32> *v = nullptr;
+    u64 n = 0;
+    switch (which) {
+    case FLYCOO_PLAN_G: wide = g1; n = 1; break;
+    case FLYCOO_PLAN_SHARD_PTR: v = &p->shard_ptr; break;
+    case FLYCOO_PLAN_SHARD_SS: v = &p->shard_ss; break;
+    case FLYCOO_PLAN_SS_SHARD_PTR: v = &p->ss_shard_ptr; break;
+    case FLYCOO_PLAN_SS_BIN_PTR: v = &p->ss_bin_ptr; break;
+    case FLYCOO_PLAN_SS_ITEMS: v = &p->ss_items; break;
+    case FLYCOO_PLAN_SHARD_BIN_PTR: v = &p->sh_bin_ptr; break;
+    case FLYCOO_PLAN_SHARD_ITEMS: v = &p->sh_items; break;
+    case FLYCOO_PLAN_K4_ITEMS: v = &p->k4_items; break;
+    case FLYCOO_PLAN_TILE_BIN_PTR_512: v = &p->tile_bin_ptr[0]; break;
+    case FLYCOO_PLAN_TILES_512: v = &p->tiles[0]; break;
+    case FLYCOO_PLAN_TILE_BIN_PTR_1024: v = &p->tile_bin_ptr[1]; break;
+    case FLYCOO_PLAN_TILES_1024: v = &p->tiles[1]; break;
+    default:
+        set_error("flycoo_plan_get: unknown array %d", which);
+        return FLYCOO_ERR_INVALID_ARG;
+    }
+    if (v) n = v->size();
+    if (h_out) {
+        if (*count < n) {
+            set_error("flycoo_plan_get: array %d has %llu entries, the buffer %llu", which, (unsigned long long)n,
+                      (unsigned long long)*count);
+            *count = n;
+            return FLYCOO_ERR_INVALID_ARG;
+        }
+        for (u64 i = 0; i < n; ++i) h_out[i] = v ? (*v)[i] : wide[i];
+    }
+    *count = n;
+    return FLYCOO_OK;
+}
+
+extern "C" void flycoo_plan_destroy(flycoo_plan p) { delete p; }

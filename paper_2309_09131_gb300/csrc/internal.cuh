@@ -77,7 +77,8 @@ struct DevBuf {
 // --------------------------------------------------------------------------
 // FLYCOO description of one mode (Section III-A)
 // --------------------------------------------------------------------------
-struct ModeMeta {
+// the host part: what plan_mode derives from the super-shard pointers
+struct ModePlan {
     u64 I = 0, m = 0, k = 0, S = 0;
     std::vector<u64> ss_ptr;              // k + 1: first position of each super-shard in L_n
     std::vector<u32> shard_ptr;           // S + 1: first position of each shard in L_n
@@ -93,6 +94,9 @@ struct ModeMeta {
     // 4 the super-shard has no other shard
     // (one set per stage-tile size, kStageTile)
     std::vector<u32> tiles[2], tile_bin_ptr[2];
+};
+
+struct ModeMeta : ModePlan {
     DevBuf d_ss_shard_ptr, d_k4, d_next;
     DevBuf d_tiles[2], d_tile_bin_ptr[2];
 };
@@ -173,6 +177,8 @@ constexpr u32 kSpinLimit = 1u << 24;
 #define FLYCOO_BLOCKS_PER_SM 3
 #endif
 constexpr int kBlocksPerSM = FLYCOO_BLOCKS_PER_SM;
+// most schedule bins (thread blocks of a fused pass) a handle or plan takes
+constexpr u32 kMaxBins = 1u << 20;
 // nonzeros of a 3-mode tensor whose factor-row gathers one thread group issues
 // together (each step of the fused kernel's inner loop)
 #ifndef FLYCOO_UNROLL3
@@ -192,7 +198,12 @@ flycoo_status exclusive_scan_u32(const u32 *in, u32 *out, u64 n, u32 *scratch, c
 flycoo_status build_flycoo(Tensor &t, const u32 *d_idx, const float *d_vals,
                            std::vector<std::vector<u32>> &ss_ptr_host, cudaStream_t s);
 
-// host bookkeeping of one mode from its super-shard pointers (api.cu)
+// the default shard size g for nnz nonzeros over `bins` schedule bins (api.cu)
+u64 default_shard_size(u64 nnz, u32 bins);
+// host only: shards, schedules, the K4 list and the tile descriptors of one
+// mode from p.ss_ptr and p.k (api.cu); no device work
+void plan_mode(ModePlan &p, u64 nnz, u64 g, u32 bins, u32 schedule);
+// plan_mode for mode n of a tensor, then the device copies of its schedule (api.cu)
 flycoo_status partition_mode(Tensor &t, int n, const std::vector<u32> &ssp, cudaStream_t s);
 
 // standalone remap step L_n -> L_{n+1} (and layout export)
