@@ -59,7 +59,8 @@ typedef enum {
  *        cache budget of Eq. 3).  Default min(I_n, 128).
  *  g     shard size in nonzeros: each super-shard is cut into runs of g
  *        consecutive nonzeros (the last one shorter).  Default: the largest
- *        power of two in [1024, 32768] that leaves about four shards per bin.
+ *        power of two in [1024, 32768] that leaves at least eight shards per
+ *        bin (1024 when none does).
  *  bins  number of schedule bins of Algorithm 3, which is also the number of
  *        thread blocks of the fused kernel; at most 2^20.  Default: 3 x the
  *        SM count.
