@@ -32,5 +32,22 @@ from ._native import (  # noqa: F401
     flycoo_timing_read,
     make_params,
 )
+from ._native import (  # noqa: F401
+    PLAN_G,
+    PLAN_K4_ITEMS,
+    PLAN_SHARD_BIN_PTR,
+    PLAN_SHARD_ITEMS,
+    PLAN_SHARD_PTR,
+    PLAN_SHARD_SS,
+    PLAN_SS_BIN_PTR,
+    PLAN_SS_ITEMS,
+    PLAN_SS_SHARD_PTR,
+    PLAN_TILE_BIN_PTR_512,
+    PLAN_TILE_BIN_PTR_1024,
+    PLAN_TILES_512,
+    PLAN_TILES_1024,
+    SCHEDULE_BLOCK_CYCLIC,
+    SCHEDULE_LPT,
+)
 from .flycoo import FlycooTensor  # noqa: F401
 from .autograd import CPOPTLoss, SpMTTKRP, cpopt_loss, spmttkrp  # noqa: F401

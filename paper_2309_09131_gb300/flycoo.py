@@ -26,7 +26,9 @@ class FlycooTensor:
 
     ``idx``: [N, nnz] coordinates (uint32/int32, numpy or torch), ``vals``:
     [nnz] float32, ``dims``: mode sizes.  ``m``, ``g``, ``bins`` are the
-    partition parameters of ``flycoo_params`` (0 = default).
+    partition parameters of ``flycoo_params`` (0 = default); ``schedule``
+    is ``SCHEDULE_LPT`` (Algorithm 3, the default) or
+    ``SCHEDULE_BLOCK_CYCLIC``.
     """
 
     def __init__(self, idx, vals, dims: Sequence[int], m: Optional[Sequence[int]] = None, g: int = 0,
