@@ -87,11 +87,11 @@ typedef struct {
     uint64_t g;                                 /* shard size used                    */
     uint32_t bins;                              /* schedule bins used                 */
     uint32_t elem_bytes;                        /* bytes of one stored nonzero        */
-    uint32_t tile;                              /* row-sorted unit, see flycoo_create */
     uint32_t schedule;                          /* FLYCOO_SCHEDULE_*                  */
     uint64_t super_shards[FLYCOO_MAX_MODES];    /* k_n = ceil(I_n / m_n)              */
     uint64_t shards[FLYCOO_MAX_MODES];          /* S_n = sum_j ceil(|SS_n,j| / g)     */
-    uint64_t fixup_super_shards[FLYCOO_MAX_MODES]; /* super-shards without exactly one shard */
+    uint64_t segments[FLYCOO_MAX_MODES];        /* runs of one super-shard's shards in one bin */
+    uint64_t fixup_super_shards[FLYCOO_MAX_MODES]; /* super-shards without exactly one segment */
     uint64_t device_bytes;                      /* device memory the handle holds     */
 } flycoo_info;
 
@@ -102,10 +102,11 @@ typedef struct flycoo_tensor *flycoo_handle;
 /* preprocessing of Section V-J).  For every mode n it computes the layout   */
 /* L_n: nonzeros ordered by their super-shard ids (ss_n, ss_{n-1}, ...,      */
 /* ss_{n+1}, input position) with ss_w = c_w div m[w], cut into super-shards */
-/* and shards, and inside each shard every run of `tile` (2048) positions    */
-/* from the shard start stably re-ordered by c_n; each nonzero's slot in     */
-/* L_{(n+1) mod N}; and the Algorithm 3 schedules.  The tensor is then       */
-/* stored in layout L_0.                                                     */
+/* and shards; each nonzero's slot in L_{(n+1) mod N}; the Algorithm 3       */
+/* schedules; and, for every stage tile the fused pass streams (runs of 512  */
+/* and of 1024 positions from each shard start), the order that sorts the    */
+/* tile stably by c_n (flycoo_export_tile_order).  The tensor is then stored */
+/* in layout L_0.                                                            */
 /*  N       number of modes, 3 <= N <= 5.                                    */
 /*  h_dims  N mode sizes, each in [1, 2^32 - 1].                             */
 /*  nnz     nonzeros, < 2^32 - 1.  0 is allowed.                             */
@@ -150,20 +151,41 @@ flycoo_status flycoo_spmttkrp(flycoo_handle h, int mode, const void *const *h_fa
                               flycoo_stream_t stream);
 
 /* ------------------------------------------------------------------------ */
+/* flycoo_all_modes_host -- Algorithm 2 end to end from host memory: copy   */
+/* the N factors in, spMTTKRP of every mode n = 0..N-1 in turn with the     */
+/* fused remap to the next layout (the tensor is first remapped to L_0 if  */
+/* it is elsewhere, and ends in L_0), each output copied back as soon as    */
+/* its pass ends; then wait for the stream and check the device error word. */
+/*  h_factors  HOST array of N HOST pointers, Y_w is I_w x R row-major in   */
+/*             `fdt` (pinned memory makes the copies asynchronous)          */
+/*  R          16, 32 or 64                                                 */
+/*  h_out      HOST array of N HOST pointers, M_n is I_n x R FP32,          */
+/*             overwritten                                                  */
+/* The first call allocates device staging for the factors and outputs     */
+/* (kept until flycoo_destroy, reallocated when a later call needs more).  */
+/* Waits for `stream`.  Errors: INVALID_ARG, LAYOUT, UNSUPPORTED, OOM,       */
+/* TIMEOUT, CUDA.                                                           */
+/* ------------------------------------------------------------------------ */
+flycoo_status flycoo_all_modes_host(flycoo_handle h, const void *const *h_factors, flycoo_dtype fdt, int R,
+                                    float *const *h_out, flycoo_stream_t stream);
+
+/* ------------------------------------------------------------------------ */
 /* flycoo_spmttkrp_static_scratch -- the paper has no counterpart; this is a  */
 /* library convenience.  Same computation, arguments, errors and results as   */
 /* flycoo_spmttkrp, but the call allocates nothing: the row blocks of the    */
-/* super-shards that span several shards go to a fixed device array inside   */
+/* super-shards split over several segments go to a fixed device array inside */
 /* the library (8 MiB per GPU, held by every GPU that loads the library until */
 /* the process exits) instead of the scratch buffer flycoo_create allocated.  */
 /* It is meant for callers that must not allocate device memory at the point  */
 /* of the call, for example code running while another allocator owns the    */
 /* GPU's free memory, or code that must not enter cudaMalloc on a time-bound  */
 /* path.  The handle itself still comes from flycoo_create, which allocates.  */
-/*  - Limit: S_mode x m_mode x R x 4 bytes must fit in 8 MiB (S_mode = shards */
-/*    and m_mode = super-shard width of the mode, see flycoo_get_info);        */
-/*    larger requests return INVALID_ARG and flycoo_last_error() gives both    */
-/*    sizes.  A larger g lowers S_mode.                                        */
+/*  - Limit: Q_mode x m_mode x R x 4 bytes must fit in 8 MiB (Q_mode =        */
+/*    segments and m_mode = super-shard width of the mode, see               */
+/*    flycoo_get_info); larger requests return INVALID_ARG and               */
+/*    flycoo_last_error() gives both sizes.  A larger g lowers Q_mode.        */
+/*  - flycoo_timing_enable does not time this pass (recording its events     */
+/*    could create them).                                                    */
 /*  - The first call on a device looks up the array's device address with     */
 /*    that device current; make that first call before any stream capture.    */
 /*  - All calls on a device share the one array and it keeps the last call's  */
@@ -176,22 +198,33 @@ flycoo_status flycoo_spmttkrp_static_scratch(flycoo_handle h, int mode, const vo
                                              flycoo_stream_t stream);
 
 /* ------------------------------------------------------------------------ */
-/* flycoo_mttkrp_adjoint -- adjoint of flycoo_spmttkrp with respect to the   */
-/* factors (the elementwise equation of Section IV is linear in each input   */
-/* factor).  For an upstream gradient G = d loss / d M_mode (I_mode x R):    */
+/* flycoo_mttkrp_adjoint -- adjoint of flycoo_spmttkrp.  The elementwise     */
+/* update of Section IV (Eq. 4) is linear in each input factor and in each   */
+/* nonzero value.  For an upstream gradient G = d loss / d M_mode            */
+/* (I_mode x R):                                                             */
 /*   dY_w = spMTTKRP_w(X, Y with Y_mode replaced by G)      for each w != mode */
+/*   dval(x) = sum_r G[c_mode(x), r] prod_{w != mode} Y_w[c_w(x), r]         */
 /* Each dY_w is one fused pass of mode w in layout L_w, so it reuses that    */
 /* mode's shards without atomics (and remaps as it goes).  The tensor is     */
-/* first remapped to L_{mode+1} if it is elsewhere and ends in L_mode.       */
-/*  h_factors   HOST array of N DEVICE FP32 factor pointers (entry mode unused) */
-/*  d_gout      I_mode x R FP32 upstream gradient                            */
+/* first remapped to L_{mode+1} if it is elsewhere and ends in L_mode; the   */
+/* value gradient is formed when the walk passes through L_0 (one gather of  */
+/* the N rows of every nonzero, FP32 products, a fixed-order sum).           */
+/*  h_factors   HOST array of N DEVICE factor pointers of type fdt, I_w x R, */
+/*              16-byte aligned (entry mode unused, may be NULL)             */
+/*  fdt         FLYCOO_F32 or FLYCOO_BF16: the type of the factors and of G  */
+/*  R           16, 32 or 64                                                 */
+/*  d_gout      I_mode x R upstream gradient of type fdt                     */
 /*  h_gfactors  HOST array of N DEVICE pointers, I_w x R FP32 outputs,       */
 /*              overwritten; NULL entries (and entry mode) are skipped       */
-/* Errors: INVALID_ARG, UNSUPPORTED (rank), CUDA.                            */
+/*  d_gvals     DEVICE nnz floats, or NULL: d_gvals[e] is dval of the        */
+/*              nonzero given at input position e of flycoo_create (the     */
+/*              caller's COO order), overwritten                            */
+/* Errors: INVALID_ARG, LAYOUT (a remapping pass gave up earlier),           */
+/* UNSUPPORTED (rank), CUDA.                                                 */
 /* ------------------------------------------------------------------------ */
-flycoo_status flycoo_mttkrp_adjoint(flycoo_handle h, int mode, const float *const *h_factors, int R,
-                                    const float *d_gout, float *const *h_gfactors,
-                                    flycoo_stream_t stream);
+flycoo_status flycoo_mttkrp_adjoint(flycoo_handle h, int mode, const void *const *h_factors,
+                                    flycoo_dtype fdt, int R, const void *d_gout,
+                                    float *const *h_gfactors, float *d_gvals, flycoo_stream_t stream);
 
 /* ------------------------------------------------------------------------ */
 /* flycoo_cpopt_grad -- weighted CP on the observed entries (CP-OPT loss):   */
@@ -296,6 +329,18 @@ flycoo_status flycoo_export_schedule(flycoo_handle h, int mode, int which, uint6
 flycoo_status flycoo_export_next(flycoo_handle h, int mode, uint32_t *d_next,
                                  flycoo_stream_t stream);
 
+/* d_order (nnz uint16, DEVICE): compute order of the stage tiles of mode    */
+/* `mode` for stage size `stage` (512 or 1024).  The stage tiles are the     */
+/* runs of `stage` positions from each shard start of L_mode (the last run   */
+/* of a shard shorter); for the tile starting at position s with length len, */
+/* d_order[s + p], p < len, is the tile-local index of the nonzero that      */
+/* comes p-th when the tile is sorted stably by its mode-`mode` coordinate.  */
+/* The fused pass accumulates each tile in this order, so every output row's */
+/* nonzeros in a tile are contiguous; the stored layout is not moved.        */
+/* Stream-ordered.  Errors: INVALID_ARG (mode, stage, NULL with nnz > 0).    */
+flycoo_status flycoo_export_tile_order(flycoo_handle h, int mode, int stage, uint16_t *d_order,
+                                       flycoo_stream_t stream);
+
 /* ------------------------------------------------------------------------ */
 /* Host-only planner: the partition and schedule step of flycoo_create for   */
 /* one mode, on its own.  It touches no device (it runs where no GPU is).    */
@@ -306,6 +351,10 @@ typedef struct flycoo_plan_s *flycoo_plan;
 /* super-shard into shards of g nonzeros, schedule the super-shards by shard */
 /* count and the shards by nonzero count (Algorithm 3, or block-cyclic), and */
 /* write the shard schedule out as the fused kernel's tile descriptors.      */
+/* Consecutive shards of one super-shard in one bin form a segment: the      */
+/* thread block accumulates the super-shard's rows across the whole segment  */
+/* and writes them once (to the output when the super-shard has a single     */
+/* segment, else to the segment's row block, which K4 sums).                 */
 /* flycoo_create runs exactly this for every mode of a handle.               */
 /*  nnz       nonzeros, < 2^32 - 1.                                          */
 /*  k         super-shards k_n = ceil(I_n / m_n), in [1, 2^32 - 2].          */
@@ -322,12 +371,14 @@ typedef struct flycoo_plan_s *flycoo_plan;
 flycoo_status flycoo_plan_create(uint64_t nnz, uint64_t k, const uint64_t *h_ss_ptr, uint64_t g,
                                  uint32_t bins, uint32_t schedule, flycoo_plan *out);
 
-/* Arrays of a plan.  S = shards, T_z = stage tiles of size 512 (z = 0) or   */
-/* 1024 (z = 1).  Schedules are CSR lists: bin b holds                       */
-/* items[bin_ptr[b] .. bin_ptr[b+1]) in assignment order.  A tile descriptor */
-/* is four values (start, len | flags << 16, super-shard, shard), flags 1 =  */
-/* first tile of its shard, 2 = last, 4 = the only shard of its super-shard; */
-/* descriptors run bin by bin in the order of the shard schedule.           */
+/* Arrays of a plan.  S = shards, Q = segments, T_z = stage tiles of size    */
+/* 512 (z = 0) or 1024 (z = 1).  Schedules are CSR lists: bin b holds        */
+/* items[bin_ptr[b] .. bin_ptr[b+1]) in assignment order.  Segments are      */
+/* numbered by super-shard, then in schedule order (bin, then position in    */
+/* the bin).  A tile descriptor is four values (start, len | flags << 16,    */
+/* super-shard, segment), flags 1 = first tile of its segment, 2 = last,     */
+/* 4 = the only segment of its super-shard; descriptors run bin by bin in    */
+/* the order of the shard schedule.                                          */
 typedef enum {
     FLYCOO_PLAN_G = 0,              /* 1: the shard size used                 */
     FLYCOO_PLAN_SHARD_PTR = 1,      /* S + 1: start of each shard, then nnz   */
@@ -337,11 +388,13 @@ typedef enum {
     FLYCOO_PLAN_SS_ITEMS = 5,       /* k                                      */
     FLYCOO_PLAN_SHARD_BIN_PTR = 6,  /* bins + 1: shard (thread-block) schedule*/
     FLYCOO_PLAN_SHARD_ITEMS = 7,    /* S                                      */
-    FLYCOO_PLAN_K4_ITEMS = 8,       /* super-shards without exactly one shard */
+    FLYCOO_PLAN_K4_ITEMS = 8,       /* super-shards without exactly one segment */
     FLYCOO_PLAN_TILE_BIN_PTR_512 = 9,   /* bins + 1, in descriptors           */
     FLYCOO_PLAN_TILES_512 = 10,         /* 4 x T_0                            */
     FLYCOO_PLAN_TILE_BIN_PTR_1024 = 11, /* bins + 1                           */
-    FLYCOO_PLAN_TILES_1024 = 12         /* 4 x T_1                            */
+    FLYCOO_PLAN_TILES_1024 = 12,        /* 4 x T_1                            */
+    FLYCOO_PLAN_SEG_SS = 13,            /* Q: super-shard of each segment     */
+    FLYCOO_PLAN_SS_SEG_PTR = 14         /* k + 1: segments of each super-shard */
 } flycoo_plan_array;
 
 /* Copy array `which` into h_out, widened to uint64.  *count is in: the     */

@@ -27,8 +27,8 @@ _LIB_PATH = os.path.join(_HERE, "liboracle.so")
 _lib = None
 
 __all__ = [
-    "build", "mttkrp", "mttkrp_rows", "sampled", "layout_order", "inverse", "partition",
-    "lpt", "lpt_bins", "round_bf16", "factors_f64", "tile_sort", "flycoo_layout", "remap",
+    "build", "mttkrp", "mttkrp_rows", "sampled", "layout_order", "layout_order_qsort", "inverse", "partition",
+    "lpt", "lpt_bins", "round_bf16", "factors_f64", "flycoo_layout", "remap",
 ]
 
 
@@ -151,10 +151,38 @@ def sampled(idx, F) -> np.ndarray:
 
 
 def layout_order(idx, mode: int, m=None) -> np.ndarray:
-    """pi_n: position -> original element of layout L_n, ordered by the
-    super-shard ids ``(c_n div m_n, c_{n-1} div m_{n-1}, ..., c_{n+1} div
-    m_{n+1}, e)`` (Sections III-A/B, reading stated in the C source).  ``m``
-    defaults to all ones (order by coordinates)."""
+    """pi_n: position -> original element of layout L_n.
+
+    Section III-B orders the tensor by the shard ids of the output mode and
+    Section III-A gives every element a super-shard in each mode.  Reading:
+    with ss_w = c_w div m_w, L_n is the input sorted by the key
+    ``(ss_n, ss_{n-1}, ..., ss_{n+1})`` (mode indices mod N), ties kept in
+    input order.  A stable library sort of that key tuple is the definition:
+    the ids are packed into one integer when they fit in 63 bits, else
+    ``np.lexsort`` takes them as separate keys.  ``m`` defaults to all ones
+    (order by coordinates)."""
+    idx = _coo(idx)
+    N, nnz = idx.shape
+    mm = np.ones(N, dtype=np.uint64) if m is None else np.asarray(m, dtype=np.uint64)
+    if nnz == 0:
+        return np.empty(0, dtype=np.uint32)
+    # keys[0] is the primary key ss_n, keys[t] = ss_{n-t}
+    keys = [idx[(mode - t) % N].astype(np.uint64) // mm[(mode - t) % N] for t in range(N)]
+    widths = [max(1, int(k.max()).bit_length()) for k in keys]
+    if sum(widths) <= 63:
+        packed = np.zeros(nnz, dtype=np.uint64)
+        for k, b in zip(keys, widths):
+            packed = (packed << np.uint64(b)) | k
+        order = np.argsort(packed, kind="stable")
+    else:
+        order = np.lexsort(keys[::-1])      # lexsort: the last key is the primary one
+    return order.astype(np.uint32)
+
+
+def layout_order_qsort(idx, mode: int, m=None) -> np.ndarray:
+    """The same order by the C library's qsort with an explicit comparator
+    on the key tuple and then the input position (a second, independent
+    coding of ``layout_order``'s definition, for small inputs)."""
     lib = _load()
     idx = _coo(idx)
     N, nnz = idx.shape
@@ -225,27 +253,11 @@ def round_bf16(x: np.ndarray) -> np.ndarray:
     return out
 
 
-def tile_sort(order, rows, shard_ptr, tile: int) -> np.ndarray:
-    """Stored order of a layout: inside each shard, every run of ``tile``
-    positions counted from the shard start is stably sorted by ``rows`` (the
-    output coordinate of each element).  The shard contents are unchanged."""
-    out = np.array(order, copy=True)
-    sp = np.asarray(shard_ptr, dtype=np.int64)
-    for q in range(sp.size - 1):
-        for a in range(int(sp[q]), int(sp[q + 1]), tile):
-            b = min(a + tile, int(sp[q + 1]))
-            seg = out[a:b]
-            out[a:b] = seg[np.argsort(rows[seg], kind="stable")]
-    return out
-
-
-def flycoo_layout(idx, dims, m: Sequence[int], g: int, nbins: int, tile: int = 512
-                  ) -> List[Dict[str, np.ndarray]]:
+def flycoo_layout(idx, dims, m: Sequence[int], g: int, nbins: int) -> List[Dict[str, np.ndarray]]:
     """Everything the FLYCOO format fixes for each mode n, from the definitions:
 
-    ``order`` (pi_n: the stored order, the super-shard key order with every
-    layout tile sorted by output coordinate), ``pos`` (its inverse: slot of
-    each element in L_n),
+    ``order`` (pi_n: the order of L_n, the super-shard key order of
+    ``layout_order``), ``pos`` (its inverse: slot of each element in L_n),
     ``ss_ptr`` and ``shard_ptr`` (Section III-A), ``shard_ss`` (super-shard
     of every shard), ``next`` (slot in L_{(n+1) mod N} of the element at each
     position of L_n: the dynamic remap of Section III-B and Algorithm 2),
@@ -257,7 +269,7 @@ def flycoo_layout(idx, dims, m: Sequence[int], g: int, nbins: int, tile: int = 5
     modes = []
     for n in range(N):
         ss_ptr, shard_ptr = partition(idx[n], int(dims[n]), int(m[n]), int(g))
-        order = tile_sort(layout_order(idx, n, m), idx[n], shard_ptr, tile)
+        order = layout_order(idx, n, m)
         starts = shard_ptr[:-1].astype(np.int64)
         ends = shard_ptr[1:].astype(np.int64)
         ss_sizes = ss_ptr[1:] - ss_ptr[:-1]

@@ -51,16 +51,18 @@ def cholesky(V: np.ndarray) -> np.ndarray:
 
 def chol_solve_rows(L: np.ndarray, B: np.ndarray) -> np.ndarray:
     """X = B V^{-1} for V = L L^T (V symmetric): solve V x_i = b_i per row i
-    by forward then backward substitution, vectorised over the rows."""
-    B = np.asarray(B, dtype=np.float64)
+    by forward then backward substitution, vectorised over the rows (the
+    rows are held transposed so each substitution step is a contiguous
+    matrix-vector product)."""
+    Bt = np.ascontiguousarray(np.asarray(B, dtype=np.float64).T)
     R = L.shape[0]
-    Z = np.empty_like(B)
+    Zt = np.empty_like(Bt)
     for j in range(R):
-        Z[:, j] = (B[:, j] - Z[:, :j] @ L[j, :j]) / L[j, j]
-    X = np.empty_like(B)
+        Zt[j] = (Bt[j] - L[j, :j] @ Zt[:j]) / L[j, j]
+    Xt = np.empty_like(Bt)
     for j in range(R - 1, -1, -1):
-        X[:, j] = (Z[:, j] - X[:, j + 1:] @ L[j + 1:, j]) / L[j, j]
-    return X
+        Xt[j] = (Zt[j] - L[j + 1:, j] @ Xt[j + 1:]) / L[j, j]
+    return np.ascontiguousarray(Xt.T)
 
 
 def _store(Y: np.ndarray, store: str) -> np.ndarray:

@@ -8,6 +8,7 @@ from ._native import (  # noqa: F401
     BF16,
     F32,
     FlycooError,
+    flycoo_all_modes_host,
     flycoo_cp_als_step,
     flycoo_cpopt_grad,
     flycoo_debug_fail_alloc_after,
@@ -18,6 +19,7 @@ from ._native import (  # noqa: F401
     flycoo_export_next,
     flycoo_export_partition,
     flycoo_export_schedule,
+    flycoo_export_tile_order,
     flycoo_get_info,
     flycoo_last_error,
     flycoo_mttkrp_adjoint,
@@ -46,6 +48,8 @@ from ._native import (  # noqa: F401
     PLAN_TILE_BIN_PTR_1024,
     PLAN_TILES_512,
     PLAN_TILES_1024,
+    PLAN_SEG_SS,
+    PLAN_SS_SEG_PTR,
     SCHEDULE_BLOCK_CYCLIC,
     SCHEDULE_LPT,
 )

@@ -42,8 +42,9 @@ class flycoo_info(ctypes.Structure):
     _fields_ = [("N", ctypes.c_int32), ("layout_mode", ctypes.c_int32), ("nnz", ctypes.c_uint64),
                 ("dims", ctypes.c_uint64 * MAX_MODES), ("m", ctypes.c_uint64 * MAX_MODES),
                 ("g", ctypes.c_uint64), ("bins", ctypes.c_uint32), ("elem_bytes", ctypes.c_uint32),
-                ("tile", ctypes.c_uint32), ("schedule", ctypes.c_uint32),
+                ("schedule", ctypes.c_uint32),
                 ("super_shards", ctypes.c_uint64 * MAX_MODES), ("shards", ctypes.c_uint64 * MAX_MODES),
+                ("segments", ctypes.c_uint64 * MAX_MODES),
                 ("fixup_super_shards", ctypes.c_uint64 * MAX_MODES), ("device_bytes", ctypes.c_uint64)]
 
 
@@ -65,7 +66,8 @@ def lib():
             "flycoo_spmttkrp_static_scratch": [P, I, P, I, I, P, I, P],
             "flycoo_remap": [P, I, P],
             "flycoo_sync": [P, P],
-            "flycoo_mttkrp_adjoint": [P, I, P, I, P, P, P],
+            "flycoo_all_modes_host": [P, P, I, I, P, P],
+            "flycoo_mttkrp_adjoint": [P, I, P, I, I, P, P, P, P],
             "flycoo_cpopt_grad": [P, P, I, P, P, P],
             "flycoo_cp_als_step": [P, P, I, I, P, P, P],
             "flycoo_get_info": [P, P],
@@ -73,6 +75,7 @@ def lib():
             "flycoo_export_partition": [P, I, P, P, P],
             "flycoo_export_schedule": [P, I, I, P, P],
             "flycoo_export_next": [P, I, P, P],
+            "flycoo_export_tile_order": [P, I, I, P, P],
             "flycoo_timing_enable": [P, I],
             "flycoo_timing_read": [P, P, P],
             "flycoo_last_error": [],
@@ -224,15 +227,23 @@ def _ptr_array(tensors, dtypes, what, skip=-1, allow_none=False):
     return arr
 
 
-def flycoo_mttkrp_adjoint(h, mode: int, factors: Sequence[torch.Tensor], gout: torch.Tensor,
-                          gfactors: Sequence[Optional[torch.Tensor]], stream=None) -> None:
+def flycoo_mttkrp_adjoint(h, mode: int, factors: Sequence[Optional[torch.Tensor]], gout: torch.Tensor,
+                          gfactors: Sequence[Optional[torch.Tensor]], gvals: Optional[torch.Tensor] = None,
+                          stream=None) -> None:
     """dY_w = spMTTKRP_w(X, Y with Y_mode := gout) into ``gfactors[w]`` (FP32;
-    None entries skipped)."""
+    None entries skipped) and, when ``gvals`` is given (float32 [nnz]), the
+    gradient with respect to each nonzero value in the input COO order.
+    ``factors`` and ``gout`` share one dtype, float32 or bfloat16."""
     R = gout.shape[1]
-    F = _ptr_array(factors, (torch.float32,), "factor", skip=mode)
-    Gp = _dev_ptr(gout, (torch.float32,), "gout")
+    dt = gout.dtype
+    if dt not in (torch.float32, torch.bfloat16):
+        raise TypeError("gout must be float32 or bfloat16")
+    F = _ptr_array(factors, (dt,), "factor", skip=mode, allow_none=True)
+    Gp = _dev_ptr(gout, (dt,), "gout")
     GF = _ptr_array(gfactors, (torch.float32,), "gradient", skip=mode, allow_none=True)
-    _check(lib().flycoo_mttkrp_adjoint(h, int(mode), F, int(R), Gp, GF, _stream(stream)))
+    Vp = _dev_ptr(gvals, (torch.float32,), "gvals") if gvals is not None else None
+    _check(lib().flycoo_mttkrp_adjoint(h, int(mode), F, BF16 if dt == torch.bfloat16 else F32, int(R), Gp, GF,
+                                       Vp, _stream(stream)))
 
 
 def flycoo_cpopt_grad(h, factors: Sequence[torch.Tensor], grads: Sequence[torch.Tensor], stream=None,
@@ -280,6 +291,26 @@ def flycoo_remap(h, next_mode: int, stream=None) -> None:
     _check(lib().flycoo_remap(h, int(next_mode), _stream(stream)))
 
 
+def flycoo_all_modes_host(h, factors: Sequence[torch.Tensor], outs: Sequence[torch.Tensor], stream=None) -> None:
+    """All-mode spMTTKRP from host memory: ``factors`` are CPU tensors
+    [I_w, R] (float32 or bfloat16, pinned for asynchronous copies), ``outs``
+    CPU float32 tensors [I_n, R], overwritten.  Waits for the stream."""
+    N = len(factors)
+    dt = factors[0].dtype
+    R = factors[0].shape[1]
+    F = (ctypes.c_void_p * N)()
+    O = (ctypes.c_void_p * N)()
+    for w in range(N):
+        f, o = factors[w], outs[w]
+        if f.is_cuda or o.is_cuda or f.dtype != dt or o.dtype != torch.float32:
+            raise TypeError("factors (one dtype) and float32 outputs must be CPU tensors")
+        if not f.is_contiguous() or not o.is_contiguous() or f.shape[1] != R or o.shape[1] != R:
+            raise ValueError("contiguous [I, R] tensors with one rank are required")
+        F[w] = ctypes.c_void_p(f.data_ptr())
+        O[w] = ctypes.c_void_p(o.data_ptr())
+    _check(lib().flycoo_all_modes_host(h, F, BF16 if dt == torch.bfloat16 else F32, int(R), O, _stream(stream)))
+
+
 def flycoo_sync(h, stream=None) -> None:
     """Wait for the stream; raise FLYCOO_ERR_TIMEOUT if a bounded device wait gave up."""
     _check(lib().flycoo_sync(h, _stream(stream)))
@@ -290,8 +321,9 @@ def flycoo_get_info(h) -> dict:
     _check(lib().flycoo_get_info(h, ctypes.byref(info)))
     N = info.N
     return dict(N=N, layout_mode=info.layout_mode, nnz=info.nnz, dims=list(info.dims[:N]),
-                m=list(info.m[:N]), g=info.g, bins=info.bins, elem_bytes=info.elem_bytes, tile=info.tile,
+                m=list(info.m[:N]), g=info.g, bins=info.bins, elem_bytes=info.elem_bytes,
                 super_shards=list(info.super_shards[:N]), shards=list(info.shards[:N]),
+                segments=list(info.segments[:N]),
                 fixup_super_shards=list(info.fixup_super_shards[:N]), device_bytes=info.device_bytes,
                 schedule=info.schedule)
 
@@ -333,6 +365,16 @@ def flycoo_export_next(h, mode: int, stream=None) -> torch.Tensor:
     return nx
 
 
+def flycoo_export_tile_order(h, mode: int, stage: int, stream=None) -> torch.Tensor:
+    """Compute order of the stage tiles of ``mode`` for stage size 512 or
+    1024 (int16 holding uint16 tile-local indexes, one per position)."""
+    nnz = flycoo_get_info(h)["nnz"]
+    out = torch.empty(nnz, dtype=torch.int16, device="cuda")
+    _check(lib().flycoo_export_tile_order(h, int(mode), int(stage), ctypes.c_void_p(out.data_ptr()),
+                                          _stream(stream)))
+    return out
+
+
 def flycoo_timing_enable(h, enable: bool = True) -> None:
     _check(lib().flycoo_timing_enable(h, 1 if enable else 0))
 
@@ -357,6 +399,8 @@ PLAN_TILE_BIN_PTR_512 = 9
 PLAN_TILES_512 = 10
 PLAN_TILE_BIN_PTR_1024 = 11
 PLAN_TILES_1024 = 12
+PLAN_SEG_SS = 13
+PLAN_SS_SEG_PTR = 14
 
 
 def flycoo_plan_create(nnz: int, ss_ptr, g: int = 0, bins: int = 1, schedule: int = SCHEDULE_LPT):

@@ -20,7 +20,7 @@ BUILD_DIR = os.path.join(ROOT, "_build")
 LIB_DIR = os.path.join(HERE, "_lib")
 LIB_PATH = os.path.join(LIB_DIR, "libflycoo.so")
 
-SOURCES = ["api.cu", "partition.cu", "fused_n3.cu", "fused_n4.cu", "fused_n5.cu", "static_scratch.cu", "als.cu"]
+SOURCES = ["api.cu", "partition.cu", "fused_n3.cu", "fused_n4.cu", "fused_n5.cu", "static_scratch.cu", "als.cu", "grad.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE,
                      "--expt-relaxed-constexpr"]

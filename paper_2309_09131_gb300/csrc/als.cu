@@ -9,13 +9,21 @@
 //   3. V = L D L^T and W = V^{-1} in FP64 (R/8 blocks, one column of W per
 //      warp); a pivot that is not positive ends the step with
 //      FLYCOO_ERR_NOT_SPD;
-//   4. Y = M_n W in FP32 (W rounded to FP32) and the column sums of squares;
-//   5. lambda_r = column 2-norm (FP64); Y_n = Y / lambda rounded to FP32, then
-//      to BF16 when the factors are stored in BF16;
+//   4. Y = M_n W with W in FP64 and the sums carried in double-float (below),
+//      and the column sums of squares of Y in FP64;
+//   5. lambda_r = column 2-norm (FP64); Y_n = Y / lambda in FP64, rounded to
+//      FP32, then to BF16 when the factors are stored in BF16;
 //   6. G_n = Y_n^T Y_n from the stored factor.
-// Gram matrices: FP32 products summed over a block's rows of one staged chunk
-// (64 or 128 rows per thread), those sums accumulated in FP64 per block and the
-// blocks summed in a fixed order.  After the last mode
+// The long sums of steps 4 and 6 (over I_n rows or R terms) are carried as
+// double-float pairs (hi, lo) of FP32 values: each product a*b is split
+// exactly into p + e with an FMA (e = fma(a, b, -p)), p is added to hi with
+// Knuth's two-sum, and the rounding errors go to lo.  A pair keeps about 46
+// significant bits, so the Gram matrices and M_n W come out with FP64-level
+// accuracy at FP32 rates (FP64 runs at a small fraction of the FP32 rate on
+// this GPU).  Every operation of a pair uses the _rn intrinsics, which the
+// compiler never contracts into FMAs.  Chunk sums of pairs are accumulated in
+// FP64, and the blocks' partials are added in a fixed order.  After the last
+// mode
 //   fit = 1 - sqrt(||X||^2 + ||Xhat||^2 - 2 <X, Xhat>) / ||X||,
 //   ||Xhat||^2 = lambda^T (hadamard_w G_w) lambda,
 //   <X, Xhat>  = sum_r lambda_r sum_i M_{N-1}[i,r] Y_{N-1}[i,r].
@@ -32,6 +40,29 @@ namespace {
 
 constexpr int kAlsThreads = 256;
 
+// (hi, lo) += a * (bhi + blo): the product a * bhi is split exactly into
+// p + e, p joins hi by two-sum, and the rounding terms (with a * blo) join lo
+__device__ __forceinline__ void df_fma(float &hi, float &lo, float a, float bhi, float blo) {
+    const float p = __fmul_rn(a, bhi);
+    const float e = __fmaf_rn(a, bhi, -p);
+    const float s = __fadd_rn(hi, p);
+    const float bb = __fsub_rn(s, hi);
+    const float t = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+    hi = s;
+    lo = __fadd_rn(lo, __fadd_rn(t, __fmaf_rn(a, blo, e)));
+}
+
+// (hi, lo) += a * b
+__device__ __forceinline__ void df_fma(float &hi, float &lo, float a, float b) {
+    const float p = __fmul_rn(a, b);
+    const float e = __fmaf_rn(a, b, -p);
+    const float s = __fadd_rn(hi, p);
+    const float bb = __fsub_rn(s, hi);
+    const float t = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+    hi = s;
+    lo = __fadd_rn(lo, __fadd_rn(t, e));
+}
+
 template <bool BF16> __device__ __forceinline__ float load_factor(const void *Y, u64 i) {
     if constexpr (BF16) return __bfloat162float(static_cast<const __nv_bfloat16 *>(Y)[i]);
     else return static_cast<const float *>(Y)[i];
@@ -46,8 +77,9 @@ __device__ __forceinline__ void block_rows(u64 I, u64 &lo, u64 &hi) {
 // Gram partials: partials[b][a*R + c] = sum over the rows of block b of Y[i,a] Y[i,c].
 // A block stages chunks of rows (32 KB of FP32) in shared memory with 16-byte
 // loads.  Thread t of row group g owns the B x B tile at (a0, c0) and sums the
-// products of the group's rows of the chunk in FP32; the chunk sums are
-// accumulated in FP64, and the groups' partials are added in group order.
+// products of the group's rows of the chunk as double-float pairs; the chunk
+// sums are accumulated in FP64, and the groups' partials are added in group
+// order.
 template <int R> struct GramCfg {
     static constexpr int B = (R >= 32) ? 4 : 2;      // register tile per thread
     static constexpr int TB = R / B;                 // tiles per matrix row
@@ -90,11 +122,11 @@ __global__ void __launch_bounds__(kAlsThreads) gram_partial_kernel(const void *Y
             for (int e = threadIdx.x; e < nr * R / 4; e += kAlsThreads) reinterpret_cast<float4 *>(rows)[e] = src[e];
         }
         __syncthreads();
-        float sum[B][B];
+        float hi[B][B], lo[B][B];
 #pragma unroll
         for (int x = 0; x < B; ++x)
 #pragma unroll
-            for (int y = 0; y < B; ++y) sum[x][y] = 0.f;
+            for (int y = 0; y < B; ++y) hi[x][y] = lo[x][y] = 0.f;
         for (int i = g; i < nr; i += NG) {
             float va[B], vc[B];
 #pragma unroll
@@ -105,12 +137,12 @@ __global__ void __launch_bounds__(kAlsThreads) gram_partial_kernel(const void *Y
 #pragma unroll
             for (int x = 0; x < B; ++x)
 #pragma unroll
-                for (int y = 0; y < B; ++y) sum[x][y] = fmaf(va[x], vc[y], sum[x][y]);
+                for (int y = 0; y < B; ++y) df_fma(hi[x][y], lo[x][y], va[x], vc[y]);
         }
 #pragma unroll
         for (int x = 0; x < B; ++x)
 #pragma unroll
-            for (int y = 0; y < B; ++y) acc[x][y] += (double)sum[x][y];
+            for (int y = 0; y < B; ++y) acc[x][y] += (double)hi[x][y] + (double)lo[x][y];
     }
     __syncthreads();
     double *gp = reinterpret_cast<double *>(rows); // [NG][R*R]
@@ -175,7 +207,7 @@ constexpr int kInvWarps = 8; // columns of the inverse per block, one per warp
 // Shared memory: V (R x R) and the pivot reciprocals (R).  After the loop the
 // strictly lower triangle of V holds L and the strictly upper one L^T.
 __global__ void __launch_bounds__(kInvWarps * 32)
-    ldl_inverse_kernel(const double *G, int N, int n, int R, float *W, u32 *status) {
+    ldl_inverse_kernel(const double *G, int N, int n, int R, double *W, u32 *status) {
     extern __shared__ double inv_smem[];
     double *V = inv_smem, *dinv = inv_smem + R * R;
     __shared__ int bad;
@@ -239,26 +271,31 @@ __global__ void __launch_bounds__(kInvWarps * 32)
         if (has0 && i0 < q) z0 -= V[q * R + i0] * wq; // V[q][i] = L[q][i] (lower)
         if (has1 && i1 < q) z1 -= V[q * R + i1] * wq;
     }
-    if (has0) W[i0 * R + c] = (float)z0;
-    if (has1) W[i1 * R + c] = (float)z1;
+    if (has0) W[i0 * R + c] = z0;
+    if (has1) W[i1 * R + c] = z1;
 }
 
-// Y = M W in FP32.  Tiles of M (16 KB) are staged in shared memory; thread t
-// computes column c = t % R of the tile's rows t/R, t/R + 256/R, ..., with
-// column c of W in registers.  Per-block column sums of squares (FP32 over a
-// tile, FP64 across tiles).
+// Y = M W with W = V^{-1} in FP64.  W is split into FP32 pairs
+// (hi, lo) = (fl32(w), fl32(w - hi)) in shared memory; tiles of M (8 KB) are
+// staged in shared memory; thread t computes column c = t % R of the tile's
+// rows t/R, t/R + 256/R, ..., each as a double-float sum over a of
+// M[i,a] * (hi + lo)[a,c] (about 46 significant bits), and stores the pair.
+// Per-block column sums of squares of the pairs' values in FP64.
 template <int R>
 __global__ void __launch_bounds__(kAlsThreads)
-    als_apply_kernel(const float *M, const float *W, float *Y, u64 I, double *colsq, const u32 *status) {
-    constexpr int ROWS = 4096 / R;
+    als_apply_kernel(const float *M, const double *W, float2 *Y, u64 I, double *colsq, const u32 *status) {
+    constexpr int ROWS = 2048 / R;
     constexpr int rstep = kAlsThreads / R;
     __shared__ __align__(16) float mt[ROWS * R];
+    __shared__ float2 wp[R * R];
     __shared__ double part[kAlsThreads];
     if (*status) return;
+    for (int e = threadIdx.x; e < R * R; e += kAlsThreads) {
+        const double w = W[e];
+        const float whi = __double2float_rn(w);
+        wp[e] = make_float2(whi, __double2float_rn(w - (double)whi));
+    }
     const int c = threadIdx.x % R, rsub = threadIdx.x / R;
-    float w[R];
-#pragma unroll
-    for (int a = 0; a < R; ++a) w[a] = W[a * R + c];
     u64 lo, hi;
     block_rows(I, lo, hi);
     double sq = 0.0;
@@ -268,22 +305,18 @@ __global__ void __launch_bounds__(kAlsThreads)
         const float4 *src = reinterpret_cast<const float4 *>(M + r0 * R);
         for (int e = threadIdx.x; e < nr * R / 4; e += kAlsThreads) reinterpret_cast<float4 *>(mt)[e] = src[e];
         __syncthreads();
-        float sq32 = 0.f;
         for (int i = rsub; i < nr; i += rstep) {
-            const float4 *m = reinterpret_cast<const float4 *>(mt + i * R);
-            float y = 0.f;
-#pragma unroll
-            for (int a4 = 0; a4 < R / 4; ++a4) {
-                const float4 v = m[a4];
-                y = fmaf(v.x, w[4 * a4 + 0], y);
-                y = fmaf(v.y, w[4 * a4 + 1], y);
-                y = fmaf(v.z, w[4 * a4 + 2], y);
-                y = fmaf(v.w, w[4 * a4 + 3], y);
+            const float *m = mt + i * R;
+            float yh = 0.f, yl = 0.f;
+#pragma unroll 8
+            for (int a = 0; a < R; ++a) {
+                const float2 w = wp[a * R + c];
+                df_fma(yh, yl, m[a], w.x, w.y);
             }
-            Y[(r0 + i) * R + c] = y;
-            sq32 = fmaf(y, y, sq32);
+            Y[(r0 + i) * R + c] = make_float2(yh, yl);
+            const double y = (double)yh + (double)yl;
+            sq = fma(y, y, sq);
         }
-        sq += (double)sq32;
     }
     part[threadIdx.x] = sq;
     __syncthreads();
@@ -294,13 +327,13 @@ __global__ void __launch_bounds__(kAlsThreads)
     }
 }
 
-// factor = Y * (1 / lambda) in FP64, rounded to FP32, then to BF16 when stored
-// so; with M set, also the per-block partials of sum_i M[i,r] factor[i,r].
-// Thread t handles the four columns 4q..4q+3, q = t % (R/4), of every
-// (256/(R/4))-th row, with 16-byte loads.
+// factor = Y * (1 / lambda) in FP64 (Y from its double-float pairs), rounded
+// to FP32, then to BF16 when stored so; with M set, also the per-block
+// partials of sum_i M[i,r] factor[i,r].  Thread t handles the four columns
+// 4q..4q+3, q = t % (R/4), of every (256/(R/4))-th row, with 16-byte loads.
 template <int R, bool BF16>
 __global__ void __launch_bounds__(kAlsThreads)
-    normalize_store_kernel(const float *Yt, const double *lambda, void *Yout, u64 I, const float *M, double *inner,
+    normalize_store_kernel(const float2 *Yt, const double *lambda, void *Yout, u64 I, const float *M, double *inner,
                            const u32 *status) {
     constexpr int Q = R / 4;
     constexpr int rstep = kAlsThreads / Q;
@@ -317,9 +350,12 @@ __global__ void __launch_bounds__(kAlsThreads)
     block_rows(I, lo, hi);
     double s[4] = {0.0, 0.0, 0.0, 0.0};
     for (u64 i = lo + rsub; i < hi; i += rstep) {
-        const float4 y = reinterpret_cast<const float4 *>(Yt)[i * Q + q];
-        float v[4] = {(float)((double)y.x * inv[0]), (float)((double)y.y * inv[1]), (float)((double)y.z * inv[2]),
-                      (float)((double)y.w * inv[3])};
+        const float4 ya = reinterpret_cast<const float4 *>(Yt)[(i * Q + q) * 2];
+        const float4 yb = reinterpret_cast<const float4 *>(Yt)[(i * Q + q) * 2 + 1];
+        const double y[4] = {(double)ya.x + (double)ya.y, (double)ya.z + (double)ya.w, (double)yb.x + (double)yb.y,
+                             (double)yb.z + (double)yb.w};
+        float v[4] = {__double2float_rn(y[0] * inv[0]), __double2float_rn(y[1] * inv[1]),
+                      __double2float_rn(y[2] * inv[2]), __double2float_rn(y[3] * inv[3])};
         if constexpr (BF16) {
             __nv_bfloat16 b[4];
 #pragma unroll
@@ -356,13 +392,13 @@ __global__ void __launch_bounds__(kAlsThreads)
 }
 
 template <int R>
-void launch_normalize_t(bool bf, const float *Yt, const double *lambda, void *Yout, u64 I, const float *M,
+void launch_normalize_t(bool bf, const float2 *Yt, const double *lambda, void *Yout, u64 I, const float *M,
                         double *inner, const u32 *status, int nblk, cudaStream_t s) {
     if (bf) normalize_store_kernel<R, true><<<nblk, kAlsThreads, 0, s>>>(Yt, lambda, Yout, I, M, inner, status);
     else normalize_store_kernel<R, false><<<nblk, kAlsThreads, 0, s>>>(Yt, lambda, Yout, I, M, inner, status);
 }
 
-void launch_normalize(int R, bool bf, const float *Yt, const double *lambda, void *Yout, u64 I, const float *M,
+void launch_normalize(int R, bool bf, const float2 *Yt, const double *lambda, void *Yout, u64 I, const float *M,
                       double *inner, const u32 *status, int nblk, cudaStream_t s) {
     switch (R) {
     case 16: launch_normalize_t<16>(bf, Yt, lambda, Yout, I, M, inner, status, nblk, s); break;
@@ -444,7 +480,7 @@ flycoo_status gram(const void *Y, bool bf16, u64 I, int R, double *G, double *gp
     return FLYCOO_OK;
 }
 
-void launch_apply(int R, const float *M, const float *W, float *Y, u64 I, double *colsq, const u32 *status,
+void launch_apply(int R, const float *M, const double *W, float2 *Y, u64 I, double *colsq, const u32 *status,
                   int nblk, cudaStream_t s) {
     switch (R) {
     case 16: als_apply_kernel<16><<<nblk, kAlsThreads, 0, s>>>(M, W, Y, I, colsq, status); break;
@@ -465,10 +501,10 @@ flycoo_status als_step(Tensor &t, void *const *F, flycoo_dtype fdt, int R, doubl
     const int nblk = 4 * t.sm_count;
     if (w.rows < maxI || w.nblk != nblk) {
         FLY_TRY(w.M.alloc(maxI * kMaxRank * sizeof(float)));
-        FLY_TRY(w.Y.alloc(maxI * kMaxRank * sizeof(float)));
+        FLY_TRY(w.Y.alloc(maxI * kMaxRank * sizeof(float2)));
         FLY_TRY(w.G.alloc((size_t)FLYCOO_MAX_MODES * kMaxRank * kMaxRank * sizeof(double)));
         FLY_TRY(w.gpart.alloc((size_t)nblk * kMaxRank * kMaxRank * sizeof(double)));
-        FLY_TRY(w.W.alloc(kMaxRank * kMaxRank * sizeof(float)));
+        FLY_TRY(w.W.alloc(kMaxRank * kMaxRank * sizeof(double)));
         FLY_TRY(w.colsq.alloc((size_t)nblk * kMaxRank * sizeof(double)));
         FLY_TRY(w.inner.alloc((size_t)nblk * kMaxRank * sizeof(double)));
         FLY_TRY(w.scal.alloc((size_t)(nblk + 4) * sizeof(double)));
@@ -510,14 +546,14 @@ flycoo_status als_step(Tensor &t, void *const *F, flycoo_dtype fdt, int R, doubl
         const u64 I = t.dims[n];
         FLY_TRY(run_pass(t, n, F, fdt, R, w.M.as<float>(), nullptr, nullptr, s));
         ldl_inverse_kernel<<<(R + kInvWarps - 1) / kInvWarps, kInvWarps * 32, (RR + R) * sizeof(double), s>>>(
-            G, N, n, R, w.W.as<float>(), status);
-        launch_apply(R, w.M.as<float>(), w.W.as<float>(), w.Y.as<float>(), I, w.colsq.as<double>(), status, nblk,
+            G, N, n, R, w.W.as<double>(), status);
+        launch_apply(R, w.M.as<float>(), w.W.as<double>(), w.Y.as<float2>(), I, w.colsq.as<double>(), status, nblk,
                      s);
         reduce_partials_kernel<<<(R + 31) / 32, 256, 0, s>>>(w.colsq.as<double>(), nblk, R, d_lambda, 1, status);
         const bool last = n == N - 1;
         float *Mlast = last ? w.M.as<float>() : nullptr;
         double *inner = last ? w.inner.as<double>() : nullptr;
-        launch_normalize(R, bf, w.Y.as<float>(), d_lambda, F[n], I, Mlast, inner, status, nblk, s);
+        launch_normalize(R, bf, w.Y.as<float2>(), d_lambda, F[n], I, Mlast, inner, status, nblk, s);
         FLY_TRY_CUDA(cudaGetLastError());
         FLY_TRY(gram(F[n], bf, I, R, G + n * RR, w.gpart.as<double>(), nblk, s));
     }

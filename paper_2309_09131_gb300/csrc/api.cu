@@ -29,11 +29,12 @@ void set_error(const char *fmt, ...) {
 void clear_error() { g_last_error.clear(); }
 
 u64 Tensor::device_bytes() const {
-    u64 b = elem[0].bytes + elem[1].bytes + partials.bytes + err.bytes + loss_part.bytes + als.bytes();
+    u64 b = elem[0].bytes + elem[1].bytes + orig.bytes + partials.bytes + err.bytes + loss_part.bytes + als.bytes() +
+            host_factors.bytes + host_outs.bytes;
     for (int n = 0; n < N; ++n) {
         const ModeMeta &m = mode[n];
-        b += m.d_ss_shard_ptr.bytes + m.d_k4.bytes + m.d_next.bytes + m.d_tiles[0].bytes + m.d_tiles[1].bytes +
-             m.d_tile_bin_ptr[0].bytes + m.d_tile_bin_ptr[1].bytes;
+        b += m.d_ss_seg_ptr.bytes + m.d_k4.bytes + m.d_next.bytes + m.d_perm[0].bytes + m.d_perm[1].bytes +
+             m.d_tiles[0].bytes + m.d_tiles[1].bytes + m.d_tile_bin_ptr[0].bytes + m.d_tile_bin_ptr[1].bytes;
     }
     return b;
 }
@@ -154,8 +155,10 @@ u64 default_shard_size(u64 nnz, u32 bins) {
 
 // Section III-A: super-shard j is cut into runs of g consecutive nonzeros
 // (shards); Algorithm 3 (or block-cyclic) schedules the super-shards by shard
-// count and the shards by nonzero count; the block schedule of the shards is
-// written out as tile descriptors for both stage-tile sizes.
+// count and the shards by nonzero count.  The shard schedule is then written
+// out as tile descriptors for both stage-tile sizes, with the shards of a bin
+// grouped into segments (runs of shards of one super-shard that follow each
+// other in the bin: a block keeps accumulating across them).
 void plan_mode(ModePlan &md, u64 nnz, u64 g, u32 bins, u32 schedule) {
     md.shard_ptr.clear();
     md.shard_ss.clear();
@@ -174,12 +177,14 @@ void plan_mode(ModePlan &md, u64 nnz, u64 g, u32 bins, u32 schedule) {
     md.ss_shard_ptr[md.k] = (u32)md.S;
     md.shard_ptr.push_back((u32)nnz);
     std::vector<u64> shard_size(md.S);
-    md.tile_ptr.clear();
+    for (int z = 0; z < 2; ++z) md.tile_ptr[z].clear();
     for (u64 q = 0; q < md.S; ++q) {
         shard_size[q] = md.shard_ptr[q + 1] - md.shard_ptr[q];
-        for (u64 p = md.shard_ptr[q]; p < md.shard_ptr[q + 1]; p += kSortTile) md.tile_ptr.push_back((u32)p);
+        for (int z = 0; z < 2; ++z)
+            for (u64 p = md.shard_ptr[q]; p < md.shard_ptr[q + 1]; p += kStageTile[z])
+                md.tile_ptr[z].push_back((u32)p);
     }
-    md.tile_ptr.push_back((u32)nnz);
+    for (int z = 0; z < 2; ++z) md.tile_ptr[z].push_back((u32)nnz);
     if (schedule == FLYCOO_SCHEDULE_BLOCK_CYCLIC) {
         block_cyclic_schedule(ss_shards.size(), bins, md.ss_bin_ptr, md.ss_items);
         block_cyclic_schedule(shard_size.size(), bins, md.sh_bin_ptr, md.sh_items);
@@ -187,6 +192,26 @@ void plan_mode(ModePlan &md, u64 nnz, u64 g, u32 bins, u32 schedule) {
         lpt_schedule(ss_shards, bins, md.ss_bin_ptr, md.ss_items);
         lpt_schedule(shard_size, bins, md.sh_bin_ptr, md.sh_items);
     }
+    // segments in schedule order (bin by bin), then numbered so that the
+    // segments of each super-shard are consecutive, in schedule order
+    std::vector<u32> seg_of_item(md.S), seg_first; // temporary numbering
+    std::vector<u32> tmp_ss;
+    for (u32 b = 0; b < bins; ++b)
+        for (u64 it = md.sh_bin_ptr[b]; it < md.sh_bin_ptr[b + 1]; ++it) {
+            const u32 j = md.shard_ss[md.sh_items[it]];
+            if (it == md.sh_bin_ptr[b] || md.shard_ss[md.sh_items[it - 1]] != j) tmp_ss.push_back(j);
+            seg_of_item[it] = (u32)tmp_ss.size() - 1;
+        }
+    md.ss_seg_ptr.assign(md.k + 1, 0);
+    for (u32 j : tmp_ss) ++md.ss_seg_ptr[j + 1];
+    for (u64 j = 0; j < md.k; ++j) md.ss_seg_ptr[j + 1] += md.ss_seg_ptr[j];
+    std::vector<u32> renum(tmp_ss.size());
+    {
+        std::vector<u32> fill(md.ss_seg_ptr.begin(), md.ss_seg_ptr.end() - 1);
+        for (size_t q = 0; q < tmp_ss.size(); ++q) renum[q] = fill[tmp_ss[q]]++;
+    }
+    md.seg_ss.assign(tmp_ss.size(), 0);
+    for (size_t q = 0; q < tmp_ss.size(); ++q) md.seg_ss[renum[q]] = tmp_ss[q];
     // tile descriptors of the block schedule, for both stage-tile sizes
     for (int z = 0; z < 2; ++z) {
         const u32 tile = kStageTile[z];
@@ -195,24 +220,28 @@ void plan_mode(ModePlan &md, u64 nnz, u64 g, u32 bins, u32 schedule) {
         md.tile_bin_ptr[z].assign((size_t)bins + 1, 0);
         for (u32 b = 0; b < bins; ++b) {
             md.tile_bin_ptr[z][b] = (u32)(td.size() / 4);
-            for (u64 it = md.sh_bin_ptr[b]; it < md.sh_bin_ptr[b + 1]; ++it) {
+            const u64 i0 = md.sh_bin_ptr[b], i1 = md.sh_bin_ptr[b + 1];
+            for (u64 it = i0; it < i1; ++it) {
                 const u32 sh = md.sh_items[it];
                 const u32 j = md.shard_ss[sh];
+                const u32 seg = renum[seg_of_item[it]];
+                const bool seg_begin = it == i0 || seg_of_item[it - 1] != seg_of_item[it];
+                const bool seg_end = it + 1 == i1 || seg_of_item[it + 1] != seg_of_item[it];
                 const u32 lo = md.shard_ptr[sh], hi = md.shard_ptr[sh + 1];
-                const u32 alone = ss_shards[j] == 1 ? 4u : 0u;
+                const u32 alone = md.ss_seg_ptr[j + 1] - md.ss_seg_ptr[j] == 1 ? 4u : 0u;
                 for (u32 p = lo; p < hi; p += tile) {
                     const u32 len = std::min<u32>(tile, hi - p);
-                    const u32 flags = (p == lo ? 1u : 0u) | (p + len == hi ? 2u : 0u) | alone;
-                    td.insert(td.end(), {p, len | (flags << 16), j, sh});
+                    const u32 flags = (seg_begin && p == lo ? 1u : 0u) | (seg_end && p + len == hi ? 2u : 0u) | alone;
+                    td.insert(td.end(), {p, len | (flags << 16), j, seg});
                 }
             }
         }
         md.tile_bin_ptr[z][bins] = (u32)(td.size() / 4);
     }
-    // K4 writes the rows of every super-shard that does not have exactly one shard
+    // K4 writes the rows of every super-shard that does not have exactly one segment
     md.k4_items.clear();
     for (u64 j = 0; j < md.k; ++j)
-        if (ss_shards[j] != 1) md.k4_items.push_back((u32)j);
+        if (md.ss_seg_ptr[j + 1] - md.ss_seg_ptr[j] != 1) md.k4_items.push_back((u32)j);
 }
 
 flycoo_status partition_mode(Tensor &t, int n, const std::vector<u32> &ssp, cudaStream_t s) {
@@ -222,7 +251,7 @@ flycoo_status partition_mode(Tensor &t, int n, const std::vector<u32> &ssp, cuda
     md.k = (I + md.m - 1) / md.m;
     md.ss_ptr.assign(ssp.begin(), ssp.end());
     plan_mode(md, t.nnz, t.g, t.bins, t.schedule);
-    FLY_TRY(upload(md.d_ss_shard_ptr, md.ss_shard_ptr, s));
+    FLY_TRY(upload(md.d_ss_seg_ptr, md.ss_seg_ptr, s));
     FLY_TRY(upload(md.d_k4, md.k4_items, s));
     for (int z = 0; z < 2; ++z) {
         FLY_TRY(upload(md.d_tiles[z], md.tiles[z], s));
@@ -240,22 +269,40 @@ flycoo_status launch_fixup(int R, const FixupArgs &a, cudaStream_t s) {
     return FLYCOO_OK;
 }
 
-// Keeps the caller's current device and switches to the handle's device.
-struct DeviceGuard {
-    int prev = -1;
-    bool ok = true;
-    explicit DeviceGuard(int dev) {
-        if (cudaGetDevice(&prev) != cudaSuccess) {
-            ok = false;
-            return;
-        }
-        if (prev != dev && cudaSetDevice(dev) != cudaSuccess) ok = false;
+FusedArgs fused_args(const Tensor &t, int mode, const void *const *F, float *d_out, bool remap, float *partials) {
+    const ModeMeta &md = t.mode[mode];
+    FusedArgs a{};
+    a.elem_in = t.elem[t.cur].p;
+    a.elem_out = remap ? t.elem[1 - t.cur].p : nullptr;
+    a.next = remap ? md.d_next.as<u32>() : nullptr;
+    for (int q = 1; q < t.N; ++q) a.Y[q - 1] = F[(mode + q) % t.N];
+    a.out = d_out;
+    for (int z = 0; z < 2; ++z) {
+        a.tiles[z] = md.d_tiles[z].as<uint4>();
+        a.tile_bin_ptr[z] = md.d_tile_bin_ptr[z].as<u32>();
+        a.perm[z] = md.d_perm[z].as<uint16_t>();
     }
-    ~DeviceGuard() {
-        int cur = -1;
-        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
-    }
-};
+    a.partials = partials;
+    a.err = t.err.as<u32>();
+    a.I_out = (u32)t.dims[mode];
+    a.m = (u32)md.m;
+    a.bins = t.bins;
+    a.wait_limit = t.wait_limit;
+    return a;
+}
+
+FixupArgs fixup_args(const Tensor &t, int mode, float *d_out, const float *partials) {
+    const ModeMeta &md = t.mode[mode];
+    FixupArgs f{};
+    f.items = md.d_k4.as<u32>();
+    f.nitems = (u32)md.k4_items.size();
+    f.ss_seg_ptr = md.d_ss_seg_ptr.as<u32>();
+    f.partials = partials;
+    f.out = d_out;
+    f.I_out = (u32)t.dims[mode];
+    f.m = (u32)md.m;
+    return f;
+}
 
 } // namespace flycoo
 
@@ -336,8 +383,8 @@ static flycoo_status create_impl(int N, const uint64_t *h_dims, uint64_t nnz, co
 
     std::vector<std::vector<u32>> ss_ptr;
     FLY_TRY(build_flycoo(*t, d_idx, d_vals, ss_ptr, s));
-    for (int n = 0; n < N; ++n) t->max_S = std::max<u64>(t->max_S, t->mode[n].S);
-    FLY_TRY(t->partials.alloc(std::max<u64>(t->max_S, 1) * t->max_rows * kMaxRank * sizeof(float)));
+    for (int n = 0; n < N; ++n) t->max_seg = std::max<u64>(t->max_seg, t->mode[n].nseg());
+    FLY_TRY(t->partials.alloc(std::max<u64>(t->max_seg, 1) * t->max_rows * kMaxRank * sizeof(float)));
     FLY_TRY(t->loss_part.alloc((size_t)t->bins * sizeof(double)));
     FLY_TRY(t->err.alloc(sizeof(u32)));
     FLY_TRY_CUDA(cudaMemsetAsync(t->err.p, 0, sizeof(u32), s));
@@ -424,30 +471,15 @@ extern "C" flycoo_status flycoo_spmttkrp(flycoo_handle h, int mode, const void *
         return FLYCOO_ERR_LAYOUT;
     }
     DeviceGuard dg(t.device);
+    FLY_TRY(dg.status(__func__));
     FLY_TRY(check_usable(t, "flycoo_spmttkrp"));
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    const ModeMeta &md = t.mode[mode];
     if (t.nnz == 0) {
         FLY_TRY_CUDA(cudaMemsetAsync(d_out, 0, (size_t)t.dims[mode] * R * sizeof(float), s));
         if (next_mode >= 0) t.layout = next_mode;
         return FLYCOO_OK;
     }
-    FusedArgs a{};
-    a.elem_in = t.elem[t.cur].p;
-    a.elem_out = next_mode >= 0 ? t.elem[1 - t.cur].p : nullptr;
-    a.next = next_mode >= 0 ? md.d_next.as<u32>() : nullptr;
-    for (int q = 1; q < t.N; ++q) a.Y[q - 1] = h_factors[(mode + q) % t.N];
-    a.out = d_out;
-    for (int z = 0; z < 2; ++z) {
-        a.tiles[z] = md.d_tiles[z].as<uint4>();
-        a.tile_bin_ptr[z] = md.d_tile_bin_ptr[z].as<u32>();
-    }
-    a.partials = t.partials.as<float>();
-    a.err = t.err.as<u32>();
-    a.I_out = (u32)t.dims[mode];
-    a.m = (u32)md.m;
-    a.bins = t.bins;
-    a.wait_limit = t.wait_limit;
+    const FusedArgs a = fused_args(t, mode, h_factors, d_out, next_mode >= 0, t.partials.as<float>());
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (t.timing) {
         FLY_TRY(next_event_pair(t, &e0, &e1));
@@ -458,14 +490,7 @@ extern "C" flycoo_status flycoo_spmttkrp(flycoo_handle h, int mode, const void *
         FLY_TRY_CUDA(cudaEventRecord(e1, s));
         t.ev_pending.push_back({e0, e1});
     }
-    FixupArgs f{};
-    f.items = md.d_k4.as<u32>();
-    f.nitems = (u32)md.k4_items.size();
-    f.ss_shard_ptr = md.d_ss_shard_ptr.as<u32>();
-    f.partials = a.partials;
-    f.out = d_out;
-    f.I_out = a.I_out;
-    f.m = a.m;
+    const FixupArgs f = fixup_args(t, mode, d_out, a.partials);
     FLY_TRY(launch_fixup(R, f, s));
     if (next_mode >= 0) {
         t.cur = 1 - t.cur;
@@ -475,6 +500,60 @@ extern "C" flycoo_status flycoo_spmttkrp(flycoo_handle h, int mode, const void *
     return FLYCOO_OK;
 }
 
+extern "C" flycoo_status flycoo_all_modes_host(flycoo_handle h, const void *const *h_factors, flycoo_dtype fdt, int R,
+                                               float *const *h_out, flycoo_stream_t stream) {
+    clear_error();
+    if (!h || !h_factors || !h_out) {
+        set_error("flycoo_all_modes_host: NULL handle, factor list or output list");
+        return FLYCOO_ERR_INVALID_ARG;
+    }
+    Tensor &t = *h;
+    if (fdt != FLYCOO_F32 && fdt != FLYCOO_BF16) {
+        set_error("flycoo_all_modes_host: unknown factor dtype %d", (int)fdt);
+        return FLYCOO_ERR_INVALID_ARG;
+    }
+    if (R != 16 && R != 32 && R != 64) {
+        set_error("flycoo_all_modes_host: rank %d not built (16, 32 or 64)", R);
+        return R > 0 ? FLYCOO_ERR_UNSUPPORTED : FLYCOO_ERR_INVALID_ARG;
+    }
+    for (int w = 0; w < t.N; ++w)
+        if (!h_factors[w] || !h_out[w]) {
+            set_error("flycoo_all_modes_host: factor or output %d is NULL", w);
+            return FLYCOO_ERR_INVALID_ARG;
+        }
+    DeviceGuard dg(t.device);
+    FLY_TRY(dg.status("flycoo_all_modes_host"));
+    FLY_TRY(check_usable(t, "flycoo_all_modes_host"));
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const size_t fb = fdt == FLYCOO_BF16 ? 2 : 4;
+    // per-mode offsets, each rounded up to 256 bytes
+    size_t foff[FLYCOO_MAX_MODES + 1] = {}, ooff[FLYCOO_MAX_MODES + 1] = {};
+    for (int w = 0; w < t.N; ++w) {
+        foff[w + 1] = foff[w] + ((t.dims[w] * R * fb + 255) & ~(size_t)255);
+        ooff[w + 1] = ooff[w] + ((t.dims[w] * R * 4 + 255) & ~(size_t)255);
+    }
+    if (t.host_factors.bytes < foff[t.N]) FLY_TRY(t.host_factors.alloc(foff[t.N]));
+    if (t.host_outs.bytes < ooff[t.N]) FLY_TRY(t.host_outs.alloc(ooff[t.N]));
+    const void *F[FLYCOO_MAX_MODES] = {};
+    for (int w = 0; w < t.N; ++w) {
+        void *d = static_cast<char *>(t.host_factors.p) + foff[w];
+        FLY_TRY_CUDA(cudaMemcpyAsync(d, h_factors[w], t.dims[w] * R * fb, cudaMemcpyHostToDevice, s));
+        F[w] = d;
+    }
+    while (t.layout != 0) {
+        FLY_TRY(launch_remap_step(t, t.layout, t.elem[t.cur].p, t.elem[1 - t.cur].p, s));
+        t.cur = 1 - t.cur;
+        t.remap_since_sync = true;
+        t.layout = (t.layout + 1) % t.N;
+    }
+    for (int n = 0; n < t.N; ++n) {
+        float *d_out = reinterpret_cast<float *>(static_cast<char *>(t.host_outs.p) + ooff[n]);
+        FLY_TRY(run_pass(t, n, F, fdt, R, d_out, nullptr, nullptr, s));
+        FLY_TRY_CUDA(cudaMemcpyAsync(h_out[n], d_out, t.dims[n] * R * 4, cudaMemcpyDeviceToHost, s));
+    }
+    return check_error_word(t, s, "flycoo_all_modes_host");
+}
+
 extern "C" flycoo_status flycoo_sync(flycoo_handle h, flycoo_stream_t stream) {
     clear_error();
     if (!h) {
@@ -482,6 +561,7 @@ extern "C" flycoo_status flycoo_sync(flycoo_handle h, flycoo_stream_t stream) {
         return FLYCOO_ERR_INVALID_ARG;
     }
     DeviceGuard dg(h->device);
+    FLY_TRY(dg.status(__func__));
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     return check_error_word(*h, s, "flycoo_sync");
 }
@@ -490,39 +570,16 @@ extern "C" flycoo_status flycoo_sync(flycoo_handle h, flycoo_stream_t stream) {
 // CP-OPT gradient pass; fused remap to the next layout; then K4.
 flycoo_status flycoo::run_pass(Tensor &t, int mode, const void *const *F, flycoo_dtype fdt, int R, float *d_out,
                                const void *Yout, double *loss_part, cudaStream_t s) {
-    const ModeMeta &md = t.mode[mode];
     if (t.nnz == 0) {
         FLY_TRY_CUDA(cudaMemsetAsync(d_out, 0, (size_t)t.dims[mode] * R * sizeof(float), s));
         t.layout = (mode + 1) % t.N;
         return FLYCOO_OK;
     }
-    FusedArgs a{};
-    a.elem_in = t.elem[t.cur].p;
-    a.elem_out = t.elem[1 - t.cur].p;
-    a.next = md.d_next.as<u32>();
-    for (int q = 1; q < t.N; ++q) a.Y[q - 1] = F[(mode + q) % t.N];
-    a.out = d_out;
-    for (int z = 0; z < 2; ++z) {
-        a.tiles[z] = md.d_tiles[z].as<uint4>();
-        a.tile_bin_ptr[z] = md.d_tile_bin_ptr[z].as<u32>();
-    }
-    a.partials = t.partials.as<float>();
-    a.err = t.err.as<u32>();
+    FusedArgs a = fused_args(t, mode, F, d_out, true, t.partials.as<float>());
     a.Yout = Yout;
     a.loss_part = loss_part;
-    a.I_out = (u32)t.dims[mode];
-    a.m = (u32)md.m;
-    a.bins = t.bins;
-    a.wait_limit = t.wait_limit;
     FLY_TRY(launch_fused(t.N, R, fdt, a, s));
-    FixupArgs f{};
-    f.items = md.d_k4.as<u32>();
-    f.nitems = (u32)md.k4_items.size();
-    f.ss_shard_ptr = md.d_ss_shard_ptr.as<u32>();
-    f.partials = a.partials;
-    f.out = d_out;
-    f.I_out = a.I_out;
-    f.m = a.m;
+    const FixupArgs f = fixup_args(t, mode, d_out, a.partials);
     FLY_TRY(launch_fixup(R, f, s));
     t.cur = 1 - t.cur;
     t.remap_since_sync = true;
@@ -549,16 +606,20 @@ static flycoo_status check_factor_ptrs(const Tensor &t, const void *const *F, in
     return FLYCOO_OK;
 }
 
-extern "C" flycoo_status flycoo_mttkrp_adjoint(flycoo_handle h, int mode, const float *const *h_factors, int R,
-                                               const float *d_gout, float *const *h_gfactors,
-                                               flycoo_stream_t stream) {
+extern "C" flycoo_status flycoo_mttkrp_adjoint(flycoo_handle h, int mode, const void *const *h_factors,
+                                               flycoo_dtype fdt, int R, const void *d_gout,
+                                               float *const *h_gfactors, float *d_gvals, flycoo_stream_t stream) {
     clear_error();
     if (!h || mode < 0 || mode >= h->N) {
         set_error("flycoo_mttkrp_adjoint: bad handle or mode");
         return FLYCOO_ERR_INVALID_ARG;
     }
     Tensor &t = *h;
-    FLY_TRY(check_factor_ptrs(t, reinterpret_cast<const void *const *>(h_factors), mode, R, "flycoo_mttkrp_adjoint"));
+    if (fdt != FLYCOO_F32 && fdt != FLYCOO_BF16) {
+        set_error("flycoo_mttkrp_adjoint: unknown factor dtype %d", (int)fdt);
+        return FLYCOO_ERR_INVALID_ARG;
+    }
+    FLY_TRY(check_factor_ptrs(t, h_factors, mode, R, "flycoo_mttkrp_adjoint"));
     if (!d_gout || (reinterpret_cast<uintptr_t>(d_gout) & 15u) || !h_gfactors) {
         set_error("flycoo_mttkrp_adjoint: d_gout / h_gfactors NULL or d_gout not 16-byte aligned");
         return FLYCOO_ERR_INVALID_ARG;
@@ -569,28 +630,43 @@ extern "C" flycoo_status flycoo_mttkrp_adjoint(flycoo_handle h, int mode, const 
             return FLYCOO_ERR_INVALID_ARG;
         }
     DeviceGuard dg(t.device);
+    FLY_TRY(dg.status("flycoo_mttkrp_adjoint"));
     FLY_TRY(check_usable(t, "flycoo_mttkrp_adjoint"));
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     // the factor list of every pass: Y_w, with the output mode's slot holding G
     const void *F[FLYCOO_MAX_MODES] = {};
-    for (int w = 0; w < t.N; ++w) F[w] = (w == mode) ? (const void *)d_gout : (const void *)h_factors[w];
-    const int first = (mode + 1) % t.N;
-    while (t.layout != first) {
+    for (int w = 0; w < t.N; ++w) F[w] = (w == mode) ? d_gout : h_factors[w];
+    // the value gradient runs when the walk below passes through L_0 (every
+    // layout is visited: from L_{mode+1} around to L_mode)
+    bool vals_done = d_gvals == nullptr;
+    auto value_grad_if_l0 = [&]() -> flycoo_status {
+        if (!vals_done && t.layout == 0) {
+            FLY_TRY(launch_value_grad(t, mode, h_factors, d_gout, fdt, R, d_gvals, s));
+            vals_done = true;
+        }
+        return FLYCOO_OK;
+    };
+    auto remap_one = [&]() -> flycoo_status {
         FLY_TRY(launch_remap_step(t, t.layout, t.elem[t.cur].p, t.elem[1 - t.cur].p, s));
         t.cur = 1 - t.cur;
         t.remap_since_sync = true;
         t.layout = (t.layout + 1) % t.N;
+        return FLYCOO_OK;
+    };
+    FLY_TRY(value_grad_if_l0());
+    const int first = (mode + 1) % t.N;
+    while (t.layout != first) {
+        FLY_TRY(remap_one());
+        FLY_TRY(value_grad_if_l0());
     }
     for (int q = 1; q < t.N; ++q) {
         const int w = (mode + q) % t.N;
         if (h_gfactors[w]) {
-            FLY_TRY(run_pass(t, w, F, FLYCOO_F32, R, h_gfactors[w], nullptr, nullptr, s));
+            FLY_TRY(run_pass(t, w, F, fdt, R, h_gfactors[w], nullptr, nullptr, s));
         } else {
-            FLY_TRY(launch_remap_step(t, w, t.elem[t.cur].p, t.elem[1 - t.cur].p, s));
-            t.cur = 1 - t.cur;
-            t.remap_since_sync = true;
-            t.layout = (w + 1) % t.N;
+            FLY_TRY(remap_one());
         }
+        FLY_TRY(value_grad_if_l0());
     }
     return FLYCOO_OK;
 }
@@ -614,6 +690,7 @@ extern "C" flycoo_status flycoo_cpopt_grad(flycoo_handle h, const float *const *
             return FLYCOO_ERR_INVALID_ARG;
         }
     DeviceGuard dg(t.device);
+    FLY_TRY(dg.status(__func__));
     FLY_TRY(check_usable(t, "flycoo_cpopt_grad"));
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const void *const *F = reinterpret_cast<const void *const *>(h_factors);
@@ -658,6 +735,7 @@ extern "C" flycoo_status flycoo_cp_als_step(flycoo_handle h, void *const *h_fact
         return FLYCOO_ERR_INVALID_ARG;
     }
     DeviceGuard dg(t.device);
+    FLY_TRY(dg.status(__func__));
     FLY_TRY(check_usable(t, "flycoo_cp_als_step"));
     return als_step(t, h_factors, fdt, R, d_lambda, h_fit, reinterpret_cast<cudaStream_t>(stream));
 }
@@ -670,6 +748,7 @@ extern "C" flycoo_status flycoo_remap(flycoo_handle h, int next_mode, flycoo_str
     }
     Tensor &t = *h;
     DeviceGuard dg(t.device);
+    FLY_TRY(dg.status(__func__));
     FLY_TRY(check_usable(t, "flycoo_remap"));
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     while (t.layout != next_mode) {
@@ -695,13 +774,13 @@ extern "C" flycoo_status flycoo_get_info(flycoo_handle h, flycoo_info *out) {
     out->g = t.g;
     out->bins = t.bins;
     out->elem_bytes = (uint32_t)(t.elem_words * 4);
-    out->tile = kSortTile;
     out->schedule = t.schedule;
     for (int n = 0; n < t.N; ++n) {
         out->dims[n] = t.dims[n];
         out->m[n] = t.mode[n].m;
         out->super_shards[n] = t.mode[n].k;
         out->shards[n] = t.mode[n].S;
+        out->segments[n] = t.mode[n].nseg();
         out->fixup_super_shards[n] = t.mode[n].k4_items.size();
     }
     out->device_bytes = t.device_bytes();
@@ -716,6 +795,7 @@ extern "C" flycoo_status flycoo_export_layout(flycoo_handle h, uint32_t *d_idx_o
         return FLYCOO_ERR_INVALID_ARG;
     }
     DeviceGuard dg(h->device);
+    FLY_TRY(dg.status(__func__));
     FLY_TRY(check_usable(*h, "flycoo_export_layout"));
     return launch_export_layout(*h, h->elem[h->cur].p, d_idx_out, d_vals_out,
                                 reinterpret_cast<cudaStream_t>(stream));
@@ -762,8 +842,24 @@ extern "C" flycoo_status flycoo_export_next(flycoo_handle h, int mode, uint32_t 
     }
     if (h->nnz == 0) return FLYCOO_OK;
     DeviceGuard dg(h->device);
+    FLY_TRY(dg.status(__func__));
     FLY_TRY_CUDA(cudaMemcpyAsync(d_next, h->mode[mode].d_next.p, h->nnz * 4, cudaMemcpyDeviceToDevice,
                                  reinterpret_cast<cudaStream_t>(stream)));
+    return FLYCOO_OK;
+}
+
+extern "C" flycoo_status flycoo_export_tile_order(flycoo_handle h, int mode, int stage, uint16_t *d_order,
+                                                  flycoo_stream_t stream) {
+    clear_error();
+    if (!h || mode < 0 || mode >= h->N || (stage != 512 && stage != 1024) || (h->nnz && !d_order)) {
+        set_error("flycoo_export_tile_order: bad handle, mode, stage (512 or 1024) or NULL output");
+        return FLYCOO_ERR_INVALID_ARG;
+    }
+    if (h->nnz == 0) return FLYCOO_OK;
+    DeviceGuard dg(h->device);
+    FLY_TRY(dg.status("flycoo_export_tile_order"));
+    FLY_TRY_CUDA(cudaMemcpyAsync(d_order, h->mode[mode].d_perm[stage == 1024 ? 1 : 0].p, h->nnz * 2,
+                                 cudaMemcpyDeviceToDevice, reinterpret_cast<cudaStream_t>(stream)));
     return FLYCOO_OK;
 }
 
@@ -784,6 +880,7 @@ extern "C" flycoo_status flycoo_timing_read(flycoo_handle h, double *h_ms, uint6
         return FLYCOO_ERR_INVALID_ARG;
     }
     DeviceGuard dg(h->device);
+    FLY_TRY(dg.status(__func__));
     double total = 0.0;
     for (auto &pr : h->ev_pending) {
         FLY_TRY_CUDA(cudaEventSynchronize(pr.second));
@@ -900,6 +997,8 @@ extern "C" flycoo_status flycoo_plan_get(flycoo_plan p, int which, uint64_t *h_o
     case FLYCOO_PLAN_TILES_512: v = &p->tiles[0]; break;
     case FLYCOO_PLAN_TILE_BIN_PTR_1024: v = &p->tile_bin_ptr[1]; break;
     case FLYCOO_PLAN_TILES_1024: v = &p->tiles[1]; break;
+    case FLYCOO_PLAN_SEG_SS: v = &p->seg_ss; break;
+    case FLYCOO_PLAN_SS_SEG_PTR: v = &p->ss_seg_ptr; break;
     default:
         set_error("flycoo_plan_get: unknown array %d", which);
         return FLYCOO_ERR_INVALID_ARG;

@@ -1,42 +1,45 @@
 // fused.cuh -- K2: spMTTKRP of one mode with the dynamic remap fused into the
 // same pass (Algorithm 2, one value of n), and K4: the fixed-order sum of the
-// row blocks of super-shards that span several shards.
+// row blocks of super-shards that the schedule splits into several segments.
 //
-// Layout.  The tensor is in layout L_n: nonzeros ordered by super-shard id
-// ss_n = c_n div m_n, cut into shards of at most g consecutive nonzeros
-// (Section III-A).  Inside a super-shard the nonzeros are ordered by the other
-// modes' super-shard ids, so the remap to L_{n+1} is a stable scatter into the
-// k_{n+1} super-shards of the next mode (a few hundred write streams rather
-// than one per output row).  Inside a shard every sort unit of kSortTile
-// positions is stored sorted by c_n, so a row's nonzeros are contiguous in it.
+// Layout.  The tensor is in layout L_n: nonzeros ordered by the key of
+// super-shard ids (ss_n, ss_{n-1}, ..., ss_{n+1}, input position) with
+// ss_w = c_w div m_w, cut into shards of at most g consecutive nonzeros
+// (Section III-A).  Under this key L_{n+1} is L_n stably sorted by ss_{n+1},
+// so the nonzeros of a tile that share (ss_{n-1}, ..., ss_{n+1}) land in one
+// contiguous run of L_{n+1}: the remap stores of a warp are mostly coalesced.
 //
 // Work decomposition.  Thread block b walks the stage tiles of the shards that
-// Algorithm 3 put in bin b (1024 positions when three such blocks fit on an SM,
-// else 512; a tile never crosses a sort unit).  A shard's super-shard owns m_n
+// Algorithm 3 put in bin b (runs of 1024 positions from a shard start when
+// three such blocks fit on an SM, else 512).  A shard's super-shard owns m_n
 // output rows, which the block accumulates in shared memory (the paper keeps
-// them in cache, Eq. 3).  One thread streams the tiles with 1-D TMA bulk copies
-// into a two-stage shared buffer on mbarriers, two tiles ahead, and publishes
-// each tile's 16-byte descriptor with it.  For each tile:
+// them in cache, Eq. 3), across all shards of that super-shard that follow
+// each other in the bin (a segment).  One thread streams the tiles with 1-D
+// TMA bulk copies into a two-stage shared buffer on mbarriers, two tiles
+// ahead: the nonzeros, their slots in L_{n+1} and the tile's compute order (a
+// precomputed u16 permutation that sorts the tile stably by output index).
+// It publishes each tile's 16-byte descriptor with it.  For each tile:
 //
 //  1. remap: every thread stores a few of the tile's nonzeros at their slots of
-//     L_{n+1} (the Store of Algorithm 2's remap step), in one burst;
-//  2. compute: each group of L lanes takes a fixed slice of the tile; its lanes
-//     split the rank dimension (16 bytes of a factor row per lane).  Per
-//     nonzero it gathers the N-1 input factor rows and adds val * Hadamard
-//     product (FP32) to a running row sum in registers.  A run of one row that
-//     lies inside the slice is added to its shared-memory accumulator by the
-//     group alone;
+//     L_{n+1} (the Store of Algorithm 2's remap step), in one burst, in
+//     layout order;
+//  2. compute: each group of L lanes takes a fixed slice of the tile in its
+//     compute order, where a row's nonzeros are contiguous; its lanes split
+//     the rank dimension (16 bytes of a factor row per lane).  Per nonzero it
+//     gathers the N-1 input factor rows and adds val * Hadamard product (FP32)
+//     to a running row sum in registers.  A run of one row that lies inside
+//     the slice is added to its shared-memory accumulator by the group alone;
 //  3. combine: a run that crosses a slice edge is summed after the block
 //     barrier, in slice order, by the group where it starts; when no run
 //     crosses an edge this step and its barrier are skipped.
 //
-// At the end of a shard the accumulator rows go straight to the output when
-// the super-shard has no other shard, else to the shard's row block, and the
-// accumulator is zeroed; K4 then sums the blocks of a super-shard in shard
-// order.  Every accumulator row is updated by one thread group at a time, in an
-// order fixed by the layout and the launch shape, so results are bitwise
-// reproducible; no atomics touch the data.  Rows without nonzeros come out as
-// zeros.
+// At the end of a segment the accumulator rows go straight to the output when
+// the super-shard has no other segment, else to the segment's row block, and
+// the accumulator is zeroed; K4 then sums the blocks of a super-shard in
+// schedule order.  Every accumulator row is updated by one thread group at a
+// time, in an order fixed by the layout and the launch shape, so results are
+// bitwise reproducible; no atomics touch the data.  Rows without nonzeros come
+// out as zeros.
 //
 // Every wait on an mbarrier is bounded; a block whose wait gives up sets the
 // error word, lets its copies in flight land (bounded) and returns.
@@ -76,16 +79,23 @@ struct FusedCfg {
     static constexpr int EQ = EW / 4;               // 16-byte chunks per stored nonzero
     static constexpr int EB = EW * 4;               // bytes per stored nonzero
     static constexpr int M = (int)kMaxSuperShardRows;
-    // shared memory: two stages (nonzeros + their next slots), the row
-    // accumulators and the slice summaries
-    static constexpr size_t stage_bytes(size_t cap) { return cap * EB + (cap + 8) * 4; }
+    // shared memory: two stages (nonzeros, their next slots and the compute
+    // order; the slot and order loads are rounded out to 16-byte boundaries),
+    // the row accumulators and the slice summaries
+    static constexpr size_t NEXT_OFF(size_t cap) { return cap * EB; }
+    static constexpr size_t PERM_OFF(size_t cap) { return cap * EB + (cap + 8) * 4; }
+    static constexpr size_t stage_bytes(size_t cap) { return PERM_OFF(cap) + (cap + 16) * 2; }
     static constexpr size_t ACC = (size_t)M * R * 4;
     static constexpr size_t SUMBUF = (size_t)G * R * 4 + (((size_t)G * 4 + 15) & ~(size_t)15);
-    // + 96 bytes: two mbarriers and four 16-byte descriptor slots
-    static constexpr size_t smem_bytes(size_t cap) { return 2 * stage_bytes(cap) + ACC + SUMBUF + 96; }
+    // + 80 bytes: four 16-byte descriptor slots and two mbarriers
+    static constexpr size_t smem_bytes(size_t cap) { return 2 * stage_bytes(cap) + ACC + SUMBUF + 80; }
     // the larger stage tile when kBlocksPerSM blocks of it fit in an SM's 228 KB
-    // (1 KB of each block is reserved by the system)
+    // (1 KB of each block is reserved by the system); FLYCOO_STAGE_TILE forces one
+#ifdef FLYCOO_STAGE_TILE
+    static constexpr int TZ = FLYCOO_STAGE_TILE == 1024 ? 1 : 0;
+#else
     static constexpr int TZ = (kBlocksPerSM * (smem_bytes(kStageTile[1]) + 1024) <= 228 * 1024) ? 1 : 0;
+#endif
     static constexpr int CAP = (int)kStageTile[TZ];
     static constexpr size_t STAGE = stage_bytes(CAP);
     static constexpr size_t SMEM = smem_bytes(CAP);
@@ -275,10 +285,10 @@ __global__ void __launch_bounds__(256, kBlocksPerSM) fused_mttkrp_remap_kernel(c
     float *acc = reinterpret_cast<float *>(smem_raw + 2 * C::STAGE);          // [M][R]
     float *hacc = acc + M * R;                                               // [G][R] head partials
     u32 *pass = reinterpret_cast<u32 *>(hacc + G * R);                       // [G]
-    uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw + 2 * C::STAGE + C::ACC + C::SUMBUF);
     // sdesc[0..1]: descriptor of the tile in each stage; sdesc[2 + (t & 1)]:
     // thread 0's look-ahead copy of the descriptor of tile t
-    uint4 *sdesc = reinterpret_cast<uint4 *>(bar + 2);
+    uint4 *sdesc = reinterpret_cast<uint4 *>(smem_raw + 2 * C::STAGE + C::ACC + C::SUMBUF);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sdesc + 4);
 
     const int tid = threadIdx.x;
     const int lane = tid & 31;
@@ -307,6 +317,7 @@ __global__ void __launch_bounds__(256, kBlocksPerSM) fused_mttkrp_remap_kernel(c
     const uint64_t pol_stream = l2_policy_evict_first();
     const uint64_t pol_factor = l2_policy_evict_last();
     const uint4 *__restrict__ tiles = a.tiles[C::TZ];
+    const uint16_t *__restrict__ gperm = a.perm[C::TZ];
     const u32 t_begin = a.tile_bin_ptr[C::TZ][blockIdx.x];
     const u32 ntile = a.tile_bin_ptr[C::TZ][blockIdx.x + 1] - t_begin;
 
@@ -320,21 +331,28 @@ __global__ void __launch_bounds__(256, kBlocksPerSM) fused_mttkrp_remap_kernel(c
     }
     __syncthreads();
 
-    // thread 0: load a tile (and its next-layout slots) into a stage.  The
-    // descriptor written to sdesc reaches the waiting threads through the
-    // release of the arrive and the acquire of their wait on the same barrier.
+    // thread 0: load a tile (its nonzeros, their next-layout slots and its
+    // compute order) into a stage.  The slot and order arrays are loaded from
+    // the 16-byte boundaries around the tile (both arrays are padded at the
+    // end).  The descriptor written to sdesc reaches the waiting threads
+    // through the release of the arrive and the acquire of their wait on the
+    // same barrier.
     auto issue = [&](int st, const uint4 d) {
         const u32 start = d.x, len = d.y & 0xffffu;
         unsigned char *sb = smem_raw + (size_t)st * C::STAGE;
         const u32 nlo = start & ~3u;
         const u32 nhi = (start + len + 3u) & ~3u;
-        u32 bytes = len * C::EB;
+        const u32 plo = start & ~7u;
+        const u32 phi = (start + len + 7u) & ~7u;
+        u32 bytes = len * C::EB + (phi - plo) * 2u;
         if (remap) bytes += (nhi - nlo) * 4u;
         sdesc[st] = d;
         fence_proxy_async_smem();
         mbar_arrive_expect_tx(&bar[st], bytes);
         tma_load_1d_hint(sb, ein + (size_t)start * C::EQ, len * C::EB, &bar[st], pol_stream);
-        if (remap) tma_load_1d_hint(sb + (size_t)CAP * C::EB, a.next + nlo, (nhi - nlo) * 4u, &bar[st], pol_stream);
+        if (remap)
+            tma_load_1d_hint(sb + C::NEXT_OFF(CAP), a.next + nlo, (nhi - nlo) * 4u, &bar[st], pol_stream);
+        tma_load_1d_hint(sb + C::PERM_OFF(CAP), gperm + plo, (phi - plo) * 2u, &bar[st], pol_stream);
     };
     if (tid == 0) {
         if (ntile > 0) issue(0, tiles[t_begin]);
@@ -362,7 +380,12 @@ __global__ void __launch_bounds__(256, kBlocksPerSM) fused_mttkrp_remap_kernel(c
         const u32 m_eff = min(a.m, a.I_out - row_base);
         const unsigned char *sb = smem_raw + (size_t)st * C::STAGE;
         const uint4 *selem = reinterpret_cast<const uint4 *>(sb);
-        const u32 *snext = reinterpret_cast<const u32 *>(sb + (size_t)CAP * C::EB) + (tstart & 3u);
+        const u32 *snext = reinterpret_cast<const u32 *>(sb + C::NEXT_OFF(CAP)) + (tstart & 3u);
+        // sperm[p]: tile-local index of the nonzero at compute position p; every
+        // read is clamped to the stage, so even the unloaded order of a tile whose
+        // wait gave up cannot index outside it
+        const uint16_t *sperm = reinterpret_cast<const uint16_t *>(sb + C::PERM_OFF(CAP)) + (tstart & 7u);
+        auto elem_at = [&](u32 p) { return min((u32)sperm[p], (u32)CAP - 1u); };
 
         // 1. remap burst
         if (remap && !timed_out) {
@@ -386,8 +409,8 @@ __global__ void __launch_bounds__(256, kBlocksPerSM) fused_mttkrp_remap_kernel(c
             }
         }
 
-        // 2. compute this group's slice [lo, hi) of the tile, which is stored
-        // sorted by row inside each sort unit.  Slices are chunk positions long
+        // 2. compute this group's slice [lo, hi) of the tile's compute order,
+        // in which each row's nonzeros are contiguous.  Slices are chunk positions long
         // (odd, so the groups of a warp read different shared-memory banks).  A
         // run of one row that lies inside the slice is added by this group
         // alone; a run that crosses a slice edge is summed in step 3.
@@ -397,12 +420,14 @@ __global__ void __launch_bounds__(256, kBlocksPerSM) fused_mttkrp_remap_kernel(c
         const u32 chunk = (tlen == (u32)CAP) ? kChunkFull : (((tlen + G - 1) / G) | 1u);
         const u32 geff = (tlen == (u32)CAP) ? kGeffFull : (tlen + chunk - 1) / chunk;
         const u32 *sw = reinterpret_cast<const u32 *>(sb); // word 0 of a stored nonzero is its row index
+        // row of the nonzero at compute position p
+        auto row_at = [&](u32 p) { return sw[(size_t)elem_at(p) * C::EW]; };
         const u32 lo = min((u32)grp * chunk, tlen);
         const u32 hi = min(lo + chunk, tlen);
         // the slice's first run continues the previous slice's row / its last run
         // continues into the next slice
-        const bool head_shared = lo > 0 && lo < hi && sw[(size_t)lo * C::EW] == sw[(size_t)(lo - 1) * C::EW];
-        const bool tail_shared = hi < tlen && lo < hi && sw[(size_t)hi * C::EW] == sw[(size_t)(hi - 1) * C::EW];
+        const bool head_shared = lo > 0 && lo < hi && row_at(lo) == row_at(lo - 1);
+        const bool tail_shared = hi < tlen && lo < hi && row_at(hi) == row_at(hi - 1);
         // every group of a warp runs the same number of steps: positions past
         // the slice end repeat the slice's last nonzero with weight 0 (same
         // row, so no run ends there), and an empty slice repeats the tile's
@@ -412,7 +437,7 @@ __global__ void __launch_bounds__(256, kBlocksPerSM) fused_mttkrp_remap_kernel(c
         float racc[VEC];
 #pragma unroll
         for (int v = 0; v < VEC; ++v) racc[v] = 0.f;
-        u32 crow = min(sw[(size_t)min(lo, last) * C::EW] - row_base, (u32)M - 1u);
+        u32 crow = min(row_at(min(lo, last)) - row_base, (u32)M - 1u);
         // the first run goes to the head slot when it continues the previous slice's row
         bool first_run = head_shared;
         auto steps = [&](u32 j0, auto count) {
@@ -421,10 +446,10 @@ __global__ void __launch_bounds__(256, kBlocksPerSM) fused_mttkrp_remap_kernel(c
             uint4 y[UU][NF][CPL];
 #pragma unroll
             for (int u = 0; u < UU; ++u) {
-                const u32 p = min(lo + j0 + u, last);
+                const u32 e = elem_at(min(lo + j0 + u, last));
 #pragma unroll
                 for (int c = 0; c < C::EQ; ++c) {
-                    const uint4 x = selem[(size_t)p * C::EQ + c];
+                    const uint4 x = selem[(size_t)e * C::EQ + c];
                     const u32 xs[4] = {x.x, x.y, x.z, x.w};
 #pragma unroll
                     for (int e = 0; e < 4; ++e)
@@ -558,8 +583,9 @@ __global__ void __launch_bounds__(256, kBlocksPerSM) fused_mttkrp_remap_kernel(c
             // the next tile's slices may hold this row: their adds wait here
             __syncthreads();
         }
-        // end of the shard: its super-shard's rows to the output (the only shard of
-        // its super-shard) or to the shard's row block, and the accumulator back to zero
+        // end of the segment: its super-shard's rows to the output (the only
+        // segment of its super-shard) or to the segment's row block, and the
+        // accumulator back to zero
         if (flags & kTileLast) {
             float4 *dst = (flags & kTileAlone) ? reinterpret_cast<float4 *>(a.out + (size_t)row_base * R)
                                                : reinterpret_cast<float4 *>(a.partials + (size_t)d.w * a.m * R);
@@ -590,10 +616,11 @@ __global__ void __launch_bounds__(256, kBlocksPerSM) fused_mttkrp_remap_kernel(c
     }
 }
 
-// K4: rows of the super-shards that do not have exactly one shard: the sum of
-// their shards' row blocks in shard order (zero for an empty super-shard).
-// Block (item, c) covers 64 consecutive floats of the super-shard's rows; its
-// four 64-thread parts take every fourth shard and are added in part order.
+// K4: rows of the super-shards that do not have exactly one segment: the sum of
+// their segments' row blocks in schedule order (zero for an empty
+// super-shard).  Block (item, c) covers 64 consecutive floats of the
+// super-shard's rows; its four 64-thread parts take every fourth block and are
+// added in part order.
 static __global__ void __launch_bounds__(256) super_shard_fixup_kernel(const FixupArgs a, u32 R) {
     __shared__ float part_sum[4][64];
     const u32 item = blockIdx.x;
@@ -603,7 +630,7 @@ static __global__ void __launch_bounds__(256) super_shard_fixup_kernel(const Fix
     const u32 nfl = m_eff * R;
     const u32 f = blockIdx.y * 64 + (threadIdx.x & 63);
     const u32 part = threadIdx.x >> 6;
-    const u32 s0 = a.ss_shard_ptr[j], s1 = a.ss_shard_ptr[j + 1];
+    const u32 s0 = a.ss_seg_ptr[j], s1 = a.ss_seg_ptr[j + 1];
     float sum = 0.f;
     if (f < nfl)
         for (u32 s = s0 + part; s < s1; s += 4) sum += a.partials[(size_t)s * a.m * R + f];

@@ -6,6 +6,7 @@
 #include <cstdint>
 #include <cstring>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "flycoo.h"
@@ -72,6 +73,34 @@ struct DevBuf {
         return FLYCOO_OK;
     }
     template <class T> T *as() const { return static_cast<T *>(p); }
+    void swap(DevBuf &o) {
+        std::swap(p, o.p);
+        std::swap(bytes, o.bytes);
+    }
+};
+
+// Makes the handle's device current for the life of the guard and restores
+// the caller's device afterwards.  status() reports a failed switch, so no
+// work is enqueued on the wrong device.
+struct DeviceGuard {
+    int prev = -1;
+    int dev = -1;
+    cudaError_t err = cudaSuccess;
+    explicit DeviceGuard(int d) : dev(d) {
+        err = cudaGetDevice(&prev);
+        if (err == cudaSuccess && prev != dev) err = cudaSetDevice(dev);
+    }
+    flycoo_status status(const char *who) const {
+        if (err != cudaSuccess) {
+            set_error("%s: could not make device %d current: %s", who, dev, cudaGetErrorString(err));
+            return FLYCOO_ERR_CUDA;
+        }
+        return FLYCOO_OK;
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
 };
 
 // --------------------------------------------------------------------------
@@ -86,28 +115,41 @@ struct ModePlan {
     std::vector<u32> ss_shard_ptr;        // k + 1: shards of super-shard j are [ss_shard_ptr[j], ss_shard_ptr[j+1])
     std::vector<u32> ss_bin_ptr, ss_items;  // Algorithm 3 over super-shards
     std::vector<u32> sh_bin_ptr, sh_items;  // Algorithm 3 over shards (kernel schedule)
-    std::vector<u32> k4_items;              // super-shards whose rows K4 writes (not exactly one shard)
-    std::vector<u32> tile_ptr;              // T + 1: layout tiles (K1 only)
+    // segments: maximal runs of shards of one super-shard that follow each
+    // other in one bin of the shard schedule.  A thread block accumulates a
+    // segment's rows in shared memory without flushing between its shards;
+    // each segment of a super-shard with several segments writes one row
+    // block, numbered so that the blocks of super-shard j are
+    // [ss_seg_ptr[j], ss_seg_ptr[j+1]) in schedule order
+    std::vector<u32> seg_ss;                // segments: super-shard of each
+    std::vector<u32> ss_seg_ptr;            // k + 1
+    std::vector<u32> k4_items;              // super-shards whose rows K4 writes (not exactly one segment)
+    std::vector<u32> tile_ptr[2];           // T_z + 1: stage tiles of each size (K1 only)
     // tile descriptors in block-schedule order (bin b: tiles [tile_bin_ptr[b],
     // tile_bin_ptr[b+1])), four words each: start, len | flags << 16,
-    // super-shard, shard; flags: 1 first tile of its shard, 2 last tile,
-    // 4 the super-shard has no other shard
+    // super-shard, segment; flags: 1 first tile of its segment, 2 last tile,
+    // 4 the super-shard has no other segment
     // (one set per stage-tile size, kStageTile)
     std::vector<u32> tiles[2], tile_bin_ptr[2];
+    u64 nseg() const { return seg_ss.size(); }
 };
 
 struct ModeMeta : ModePlan {
-    DevBuf d_ss_shard_ptr, d_k4, d_next;
+    DevBuf d_ss_seg_ptr, d_k4, d_next;
+    // compute order of each stage tile (u16 per position, one array per stage
+    // size): entry p of a tile is the tile-local index of the nonzero at rank p
+    // when the tile is stably sorted by output index
+    DevBuf d_perm[2];
     DevBuf d_tiles[2], d_tile_bin_ptr[2];
 };
 
 // CP-ALS workspace (als.cu), allocated by the first flycoo_cp_als_step
 struct AlsWork {
     DevBuf M;       // max_n I_n x kMaxRank FP32: spMTTKRP of the mode being updated
-    DevBuf Y;       // max_n I_n x kMaxRank FP32: M V^{-1} before normalisation
+    DevBuf Y;       // max_n I_n x kMaxRank double-float pairs: M V^{-1} before normalisation
     DevBuf G;       // N x R x R FP64 Gram matrices of the stored factors
     DevBuf gpart;   // per-block Gram partials
-    DevBuf W;       // R x R FP32 inverse of the normal-equation matrix
+    DevBuf W;       // R x R FP64 inverse of the normal-equation matrix
     DevBuf colsq;   // per-block column sums of squares
     DevBuf inner;   // per-block partials of <X, Xhat>
     DevBuf scal;    // small FP64 results (||X||^2, fit) and the status word
@@ -132,16 +174,20 @@ struct Tensor {
     int layout = 0;     // current layout mode
     int elem_words = 4; // 32-bit words per stored nonzero
     int cur = 0;        // which element buffer holds the current layout
-    u64 max_S = 0;
+    u64 max_seg = 0;   // max over modes of the segment count (row blocks of scratch)
     DevBuf elem[2];
+    DevBuf orig;        // nnz u32: input (COO) position of the nonzero at each position of L_0
     u64 max_rows = 0;   // max over modes of min(m_n, I_n): rows of a super-shard
-    DevBuf partials;    // max_S x max_rows x kMaxRank floats: one row block per shard
+    DevBuf partials;    // max_seg x max_rows x kMaxRank floats: one row block per segment
     DevBuf err;         // device error word: bit 0 = a bounded device wait gave up
     DevBuf loss_part;   // bins doubles: per-block CP-OPT loss partials
     u32 wait_limit = 0;            // mbarrier polls before a fused pass gives up (set by create)
     bool remap_since_sync = false; // a remapping pass was enqueued since the last error-word check
     bool poisoned = false;         // a remapping pass gave up: the layout is undefined
     AlsWork als;
+    // device staging of flycoo_all_modes_host (allocated by its first call):
+    // the factors (sum_w I_w x R x factor bytes) and the outputs (sum_n I_n x R FP32)
+    DevBuf host_factors, host_outs;
     ModeMeta mode[FLYCOO_MAX_MODES];
     // kernel timing
     bool timing = false;
@@ -155,18 +201,11 @@ constexpr int kMaxRank = 64;
 // largest super-shard width m_n: the fused kernel keeps a super-shard's output
 // rows (m_n x R FP32) in shared memory
 constexpr u32 kMaxSuperShardRows = 128;
-// sort unit: inside a shard, each run of kSortTile positions (counted from the
-// shard start) is stored sorted by output index (K1), so a row's nonzeros are
-// contiguous within it
-#ifndef FLYCOO_SORT_TILE
-#define FLYCOO_SORT_TILE 2048
-#endif
-constexpr u32 kSortTile = FLYCOO_SORT_TILE;
-// stage tiles: the fused kernel streams a shard one stage tile at a time, 1024
-// positions when three blocks of that size fit on an SM, else 512; both nest
-// inside sort units, and the schedule is described for both sizes
+// stage tiles: the fused kernel streams a shard one stage tile at a time (runs
+// of 1024 positions from the shard start when three blocks of that size fit on
+// an SM, else 512) and computes each tile in row order through its
+// precomputed permutation; the schedule and the permutations exist for both sizes
 constexpr u32 kStageTile[2] = {512u, 1024u};
-static_assert(kSortTile % 1024u == 0, "a sort unit is a whole number of stage tiles");
 // iteration limit of every device-side wait (mbarrier polls); ~0.1-1 s
 constexpr u32 kSpinLimit = 1u << 24;
 
@@ -222,7 +261,8 @@ struct FusedArgs {
     float *out;
     const uint4 *tiles[2];     // tile descriptors, block-schedule order, per stage-tile size
     const u32 *tile_bin_ptr[2]; // bins + 1, per stage-tile size
-    float *partials;           // row block of shard s at s * m * R
+    const uint16_t *perm[2];   // compute order of each stage tile, per stage-tile size
+    float *partials;           // row block of segment s at s * m * R
     u32 *err;                  // device error word
     const void *Yout;          // CP-OPT pass: the output mode's factor (nullptr: plain spMTTKRP)
     double *loss_part;         // CP-OPT pass: per-block half sum of squared residuals (nullable)
@@ -235,7 +275,7 @@ struct FusedArgs {
 struct FixupArgs {
     const u32 *items;          // super-shards K4 writes
     u32 nitems;
-    const u32 *ss_shard_ptr;
+    const u32 *ss_seg_ptr;     // row blocks of super-shard j: [ss_seg_ptr[j], ss_seg_ptr[j+1])
     const float *partials;
     float *out;
     u32 I_out;
@@ -243,6 +283,11 @@ struct FixupArgs {
 };
 
 flycoo_status launch_fused(int N, int R, flycoo_dtype dt, const FusedArgs &a, cudaStream_t s);
+// the arguments of a fused pass of `mode` in its layout (api.cu): factors F
+// (N pointers, entry `mode` unused), output d_out, remap to the next layout or
+// not, row blocks of multi-segment super-shards in `partials`
+FusedArgs fused_args(const Tensor &t, int mode, const void *const *F, float *d_out, bool remap, float *partials);
+FixupArgs fixup_args(const Tensor &t, int mode, float *d_out, const float *partials);
 // one fused pass of `mode` in its layout (K2 + K4), leaving the tensor in L_{mode+1}:
 // spMTTKRP into d_out, or with Yout set the CP-OPT gradient pass (api.cu)
 flycoo_status run_pass(Tensor &t, int mode, const void *const *F, flycoo_dtype fdt, int R, float *d_out,
@@ -255,6 +300,11 @@ flycoo_status check_error_word(Tensor &t, cudaStream_t s, const char *who);
 flycoo_status als_step(Tensor &t, void *const *F, flycoo_dtype fdt, int R, double *d_lambda, double *h_fit,
                        cudaStream_t s);
 flycoo_status launch_fixup(int R, const FixupArgs &a, cudaStream_t s);
+// gradient of spMTTKRP_mode with respect to the nonzero values for the upstream
+// gradient G (I_mode x R, type fdt): d_gvals[e] for every input position e; the
+// tensor must be in L_0 (grad.cu)
+flycoo_status launch_value_grad(const Tensor &t, int mode, const void *const *Y, const void *G, flycoo_dtype fdt,
+                                int R, float *d_gvals, cudaStream_t s);
 bool fused_supported(int N, int R, flycoo_dtype dt);
 
 // launchers implemented per mode count (fused_n3.cu, fused_n4.cu, fused_n5.cu)

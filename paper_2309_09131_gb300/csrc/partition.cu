@@ -6,11 +6,13 @@
 // this cyclic key, L_{n+1} is exactly L_n stably sorted by ss_{n+1} alone, and
 // L_0 is the input order stably sorted by ss_1, ss_2, ..., ss_{N-1} and
 // finally ss_0.  K1 therefore runs 2N-1 stable sorts, each a few 8-bit LSD
-// radix passes (histogram, exclusive scan, stable scatter).  The stored order
-// then sorts every sort unit (kSortTile positions of a shard) by output
-// index, stably, so the fused kernel finds each row of a tile contiguous.  Every
-// step is integer work with no atomics on the data path, so the layouts,
-// pointers and remap permutations are bit-exact and deterministic.  There is
+// radix passes (histogram, exclusive scan, stable scatter).  The tensor is
+// stored in exactly this order.  Separately, for every stage tile of both
+// sizes, K1 records the tile's compute order: the permutation that sorts the
+// tile stably by output index, so the fused kernel finds each row of a tile
+// contiguous without moving the stored nonzeros.  Every step is integer work
+// with no atomics on the data path, so the layouts, pointers, remap
+// permutations and compute orders are bit-exact and deterministic.  There is
 // no spin-wait anywhere: the scan is a plain reduce-then-scan.
 #include "internal.cuh"
 
@@ -315,11 +317,12 @@ __global__ void export_layout_kernel(const u32 *elem, int ew, int N, int layout,
     }
 }
 
-// Sort units: inside every shard, runs of kSortTile positions (from the
-// shard start) are stored sorted by output index (stable).  One block per
-// tile: per-warp row counts, a scan, then stable ranks from __match_any_sync.
+// Compute order of the stage tiles: for the tile [start, start + len) of a
+// layout, perm_out[start + p] = the tile-local index of the nonzero that comes
+// p-th when the tile is sorted stably by output index.  One block per tile:
+// per-warp row counts, a scan, then stable ranks from __match_any_sync.
 __global__ void __launch_bounds__(256)
-    tile_sort_kernel(const u32 *pi_in, u32 *pi_out, const u32 *tile_ptr, const u32 *coord, u32 m) {
+    tile_order_kernel(const u32 *pi_in, const u32 *tile_ptr, const u32 *coord, u32 m, uint16_t *perm_out) {
     constexpr int W = 8;
     constexpr int M = (int)kMaxSuperShardRows;
     __shared__ u32 cnt[W][M];
@@ -377,7 +380,7 @@ __global__ void __launch_bounds__(256)
         __syncwarp();
         if (v && (peers & lt) == 0) cnt[warp][lr] += __popc(peers);
         __syncwarp();
-        if (v && pos < len) pi_out[start + pos] = e;
+        if (v && pos < len) perm_out[start + pos] = (uint16_t)i;
     }
 }
 
@@ -473,18 +476,23 @@ flycoo_status build_flycoo(Tensor &t, const u32 *d_idx, const float *d_vals,
     FLY_TRY_CUDA(cudaStreamSynchronize(s));
     for (int n = 0; n < N; ++n) FLY_TRY(partition_mode(t, n, ss_ptr_host[n], s));
 
-    // 4. inside each layout tile, order the positions by output index (stable)
-    for (int n = 0; n < N && nnz; ++n) {
-        const std::vector<u32> &tp = t.mode[n].tile_ptr;
-        DevBuf d_tp;
-        FLY_TRY(d_tp.alloc(tp.size() * 4));
-        FLY_TRY_CUDA(cudaMemcpyAsync(d_tp.p, tp.data(), tp.size() * 4, cudaMemcpyHostToDevice, s));
-        tile_sort_kernel<<<(unsigned)(tp.size() - 1), 256, 0, s>>>(pi[n].as<u32>(), vtmp, d_tp.as<u32>(),
-                                                                    d_idx + (u64)n * nnz, (u32)t.mode[n].m);
-        FLY_TRY_CUDA(cudaGetLastError());
-        FLY_TRY_CUDA(cudaMemcpyAsync(pi[n].p, vtmp, nnz * 4, cudaMemcpyDeviceToDevice, s));
-        FLY_TRY_CUDA(cudaStreamSynchronize(s)); // d_tp goes out of scope
-    }
+    // 4. compute order of every stage tile of both sizes (stable sort by output index)
+    for (int n = 0; n < N; ++n)
+        for (int z = 0; z < 2; ++z) {
+            // +32 bytes: tile loads round the order range out to 16-byte boundaries
+            FLY_TRY(t.mode[n].d_perm[z].alloc(nnz * 2 + 32));
+            FLY_TRY_CUDA(cudaMemsetAsync(t.mode[n].d_perm[z].p, 0, nnz * 2 + 32, s));
+            const std::vector<u32> &tp = t.mode[n].tile_ptr[z];
+            if (!nnz) continue;
+            DevBuf d_tp;
+            FLY_TRY(d_tp.alloc(tp.size() * 4));
+            FLY_TRY_CUDA(cudaMemcpyAsync(d_tp.p, tp.data(), tp.size() * 4, cudaMemcpyHostToDevice, s));
+            tile_order_kernel<<<(unsigned)(tp.size() - 1), 256, 0, s>>>(
+                pi[n].as<u32>(), d_tp.as<u32>(), d_idx + (u64)n * nnz, (u32)t.mode[n].m,
+                t.mode[n].d_perm[z].as<uint16_t>());
+            FLY_TRY_CUDA(cudaGetLastError());
+            FLY_TRY_CUDA(cudaStreamSynchronize(s)); // d_tp goes out of scope
+        }
 
     // 5. remap permutations: next_n[p] = pos_{n+1}[pi_n[p]]
     {
@@ -513,6 +521,9 @@ flycoo_status build_flycoo(Tensor &t, const u32 *d_idx, const float *d_vals,
     t.cur = 0;
     t.layout = 0;
     FLY_TRY_CUDA(cudaStreamSynchronize(s));
+    // the input position of every nonzero of L_0 stays with the handle (the
+    // value gradient is written in input order)
+    t.orig.swap(pi[0]);
     return FLYCOO_OK;
 }
 

@@ -1,7 +1,9 @@
 // static_scratch.cu -- flycoo_spmttkrp_static_scratch: the fused spMTTKRP +
-// remap pass with its scratch (the per-shard row blocks of super-shards that
-// span several shards) in a fixed, file-scope device array instead of the
-// buffer that flycoo_create allocates for the handle.
+// remap pass with its scratch (the row blocks of super-shards whose shards
+// fall into several segments of the schedule) in a fixed, file-scope device
+// array instead of the buffer that flycoo_create allocates for the handle.
+// The pass is not timed by flycoo_timing_enable: recording events could
+// create them, and this entry point creates nothing.
 //
 // Host code must not pass g_static_scratch itself to a kernel: on the host that
 // name is only a stand-in object, not a device address.  The device address is
@@ -24,7 +26,9 @@ constexpr int kMaxDevices = 64;
 std::mutex g_scratch_mu;
 float *g_scratch_dev_ptr[kMaxDevices] = {};
 
-// Device address of g_static_scratch on device `dev` (which must be current).
+// Device address of g_static_scratch on device `dev`, which the caller has
+// made current.  The address is cached only after the current device has been
+// read back as `dev`, so a lookup can never be filed under the wrong device.
 flycoo_status static_scratch_address(int dev, float **out) {
     if (dev < 0 || dev >= kMaxDevices) {
         set_error("flycoo_spmttkrp_static_scratch: device %d outside [0, %d)", dev, kMaxDevices);
@@ -32,8 +36,15 @@ flycoo_status static_scratch_address(int dev, float **out) {
     }
     std::lock_guard<std::mutex> lock(g_scratch_mu);
     if (!g_scratch_dev_ptr[dev]) {
+        int cur = -1;
+        cudaError_t e = cudaGetDevice(&cur);
+        if (e != cudaSuccess || cur != dev) {
+            set_error("flycoo_spmttkrp_static_scratch: device %d is not current (current %d: %s)", dev, cur,
+                      cudaGetErrorString(e));
+            return FLYCOO_ERR_CUDA;
+        }
         void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+        e = cudaGetSymbolAddress(&p, g_static_scratch);
         if (e != cudaSuccess || p == nullptr) {
             set_error("flycoo_spmttkrp_static_scratch: cudaGetSymbolAddress failed on device %d: %s", dev,
                       cudaGetErrorString(e));
@@ -44,17 +55,6 @@ flycoo_status static_scratch_address(int dev, float **out) {
     *out = g_scratch_dev_ptr[dev];
     return FLYCOO_OK;
 }
-
-struct ScratchDeviceGuard {
-    int prev = -1;
-    explicit ScratchDeviceGuard(int dev) {
-        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
-    }
-    ~ScratchDeviceGuard() {
-        int cur = -1;
-        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
-    }
-};
 
 } // namespace
 } // namespace flycoo
@@ -104,17 +104,18 @@ extern "C" flycoo_status flycoo_spmttkrp_static_scratch(flycoo_handle h, int mod
         return FLYCOO_ERR_LAYOUT;
     }
     const ModeMeta &md = t.mode[mode];
-    // one row block (m rows x R floats) per shard
-    const size_t need = (size_t)md.S * (size_t)md.m * (size_t)R;
+    // one row block (m rows x R floats) per segment of the mode's schedule
+    const size_t need = (size_t)md.nseg() * (size_t)md.m * (size_t)R;
     if (need > kStaticScratchFloats) {
-        set_error("flycoo_spmttkrp_static_scratch: mode %d has %llu shards of %llu-row super-shards; rank %d "
+        set_error("flycoo_spmttkrp_static_scratch: mode %d has %llu row blocks of %llu-row super-shards; rank %d "
                   "needs %zu bytes of scratch, the static scratch holds %zu bytes (use flycoo_spmttkrp or a "
                   "larger shard size g)",
-                  mode, (unsigned long long)md.S, (unsigned long long)md.m, R, need * sizeof(float),
+                  mode, (unsigned long long)md.nseg(), (unsigned long long)md.m, R, need * sizeof(float),
                   kStaticScratchBytes);
         return FLYCOO_ERR_INVALID_ARG;
     }
-    ScratchDeviceGuard dg(t.device);
+    DeviceGuard dg(t.device);
+    FLY_TRY(dg.status("flycoo_spmttkrp_static_scratch"));
     FLY_TRY(check_usable(t, "flycoo_spmttkrp_static_scratch"));
     float *scratch = nullptr;
     FLY_TRY(static_scratch_address(t.device, &scratch));
@@ -124,32 +125,9 @@ extern "C" flycoo_status flycoo_spmttkrp_static_scratch(flycoo_handle h, int mod
         if (next_mode >= 0) t.layout = next_mode;
         return FLYCOO_OK;
     }
-    FusedArgs a{};
-    a.elem_in = t.elem[t.cur].p;
-    a.elem_out = next_mode >= 0 ? t.elem[1 - t.cur].p : nullptr;
-    a.next = next_mode >= 0 ? md.d_next.as<u32>() : nullptr;
-    for (int q = 1; q < t.N; ++q) a.Y[q - 1] = h_factors[(mode + q) % t.N];
-    a.out = d_out;
-    for (int z = 0; z < 2; ++z) {
-        a.tiles[z] = md.d_tiles[z].as<uint4>();
-        a.tile_bin_ptr[z] = md.d_tile_bin_ptr[z].as<u32>();
-    }
-    a.partials = scratch;
-    a.err = t.err.as<u32>();
-    a.I_out = (u32)t.dims[mode];
-    a.m = (u32)md.m;
-    a.bins = t.bins;
-    a.wait_limit = t.wait_limit;
+    const FusedArgs a = fused_args(t, mode, h_factors, d_out, next_mode >= 0, scratch);
     FLY_TRY(launch_fused(t.N, R, fdt, a, s));
-    FixupArgs f{};
-    f.items = md.d_k4.as<u32>();
-    f.nitems = (u32)md.k4_items.size();
-    f.ss_shard_ptr = md.d_ss_shard_ptr.as<u32>();
-    f.partials = a.partials;
-    f.out = d_out;
-    f.I_out = a.I_out;
-    f.m = a.m;
-    FLY_TRY(launch_fixup(R, f, s));
+    FLY_TRY(launch_fixup(R, fixup_args(t, mode, d_out, scratch), s));
     if (next_mode >= 0) {
         t.cur = 1 - t.cur;
         t.remap_since_sync = true;

@@ -147,6 +147,9 @@ class FlycooTensor:
     def export_next(self, mode: int, stream=None) -> torch.Tensor:
         return nat.flycoo_export_next(self.h, mode, stream)
 
+    def export_tile_order(self, mode: int, stage: int, stream=None) -> torch.Tensor:
+        return nat.flycoo_export_tile_order(self.h, mode, stage, stream)
+
     # ---------------------------------------------------------------- timing
     def timing_enable(self, enable: bool = True) -> None:
         nat.flycoo_timing_enable(self.h, enable)

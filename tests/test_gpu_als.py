@@ -4,13 +4,18 @@ with the same storage rounding, plus properties that fix the result
 independently of the oracle: exact recovery of a planted dense CP tensor,
 monotone fit, the NOT_SPD status, determinism and the layout cycle.
 
-Tolerances.  The update solves Y_n = M_n V_n^{-1}; a relative error e in
-M_n (the spMTTKRP bar is 1e-5 in FP32) reaches Y_n amplified by at most the
-condition number kappa(V_n), and the N Gauss-Seidel updates add up, so FP32
-factors and lambda are held to 1e-5 * N * max_n kappa(V_n).  The fit moves
-by at most that relative error of the three terms of the squared residual,
-divided by d(resid^2)/d(fit) = 2 resid ||X||.  BF16 storage is held to the
-BF16 bar of 1e-2."""
+Tolerances.
+* The solve itself: given the same M (the GPU's own spMTTKRP, which the
+  fused pass reproduces bit for bit), the update Y = M V^{-1} / lambda is
+  FP64-accurate, so the stored FP32 factor matches the oracle's FP64 solve
+  rounded to FP32 to within 1e-6 (a few last-place differences) even at
+  kappa(V) >= 1e5; an FP32 inverse would miss by kappa * 2^-24 ~ 1e-2.
+* A whole step against the oracle: the only error left is the FP32
+  spMTTKRP (relative 1e-5 at most, about 1e-6 in practice), which the solve
+  amplifies by at most kappa(V).  The cases here have kappa(V) <= 50 (checked
+  from the oracle's iterates), and FP32 factors and lambda are held to a
+  fixed 1e-4.
+* BF16 storage is held to the BF16 bar of 1e-2."""
 import math
 
 import numpy as np
@@ -74,6 +79,9 @@ def _run_case(P, idx, vals, dims, facs, store, **kw):
     return T, Y, got, to_np(lam), fit, start, Yo, lamo, fito
 
 
+ALS_TOL = 1e-4
+
+
 @pytest.mark.parametrize("dims,nnz,R,law,g,bins", [
     ((300, 200, 250), 40_000, 16, "zipf", 1000, 41),
     ((300, 200, 250), 40_000, 32, "uniform", 700, 64),
@@ -86,15 +94,42 @@ def test_als_step_fp32_matches_oracle(P, dims, nnz, R, law, g, bins):
     idx, vals = random_coo(dims, nnz, seed=11, law=law, value_law="lognormal")
     facs = make_factors(dims, R, "normal", seed=11)
     T, Y, got, lam, fit, start, Yo, lamo, fito = _run_case(P, idx, vals, dims, facs, "f32", g=g, bins=bins)
-    tol = 1e-5 * N * _kappa_max(start, Yo)
+    assert _kappa_max(start, Yo) <= 50
     for n in range(N):
-        assert rel_fro(got[n], Yo[n]) <= tol, (n, rel_fro(got[n], Yo[n]), tol)
-    assert rel_fro(lam, lamo) <= tol
+        assert rel_fro(got[n], Yo[n]) <= ALS_TOL, (n, rel_fro(got[n], Yo[n]))
+    assert rel_fro(lam, lamo) <= ALS_TOL
     inner = float(lamo @ np.sum(oracle.mttkrp(idx, vals, Yo, N - 1, dims) * Yo[N - 1], axis=0))
-    assert abs(fit - fito) <= _fit_tol(vals, Yo, lamo, inner, tol) + 1e-12, (fit, fito)
+    assert abs(fit - fito) <= _fit_tol(vals, Yo, lamo, inner, ALS_TOL) + 1e-12, (fit, fito)
     # columns of every updated factor have unit 2-norm
     for n in range(N):
         np.testing.assert_allclose(np.linalg.norm(got[n], axis=0), 1.0, rtol=1e-5)
+
+
+def test_als_update_solve_is_fp64_accurate(P):
+    # nearly collinear columns make V_0 = G_1 * G_2 ill-conditioned; given the
+    # GPU's own M_0, the update must equal the FP64 solve rounded to FP32
+    dims = (400, 300, 200)
+    R = 16
+    idx, vals = random_coo(dims, 30_000, seed=24, law="zipf", value_law="lognormal")
+    rng = np.random.default_rng(24)
+    facs = make_factors(dims, R, "normal", seed=24)
+    for w in (1, 2):
+        base = rng.standard_normal((dims[w], 1))
+        facs[w] = (base + 3e-3 * rng.standard_normal((dims[w], R))).astype(np.float32)
+    Y64 = [f.astype(np.float64) for f in facs]
+    V = (Y64[1].T @ Y64[1]) * (Y64[2].T @ Y64[2])
+    assert np.linalg.cond(V) >= 1e5
+    T = P.FlycooTensor(idx, vals, dims, g=700, bins=31)
+    Y = [torch.from_numpy(f).cuda() for f in facs]
+    M0 = to_np(T.spmttkrp(0, Y, remap=False)).astype(np.float64)
+    Yn = cp.chol_solve_rows(cp.cholesky(V), M0)
+    lam0 = np.sqrt(np.sum(Yn * Yn, axis=0))
+    want = (Yn / lam0).astype(np.float32)
+    T.cp_als_step(Y)
+    got = to_np(Y[0])
+    assert rel_fro(got, want) <= 1e-6, rel_fro(got, want)
+    # almost every element is the same FP32 number
+    assert np.mean(got == want) >= 0.99
 
 
 @pytest.mark.parametrize("dims,nnz,R", [((300, 200, 250), 40_000, 32), ((40, 50, 30, 20), 20_000, 16)])
@@ -109,19 +144,66 @@ def test_als_step_bf16_matches_oracle(P, dims, nnz, R):
     assert fit == pytest.approx(fito, abs=1e-2)
 
 
+SKEWED_DIMS = (20_000, 200_000, 500_000)
+SKEWED_LAWS = (("hot", 10, 0.5), ("uniform",), ("uniform",))
+
+
 def test_als_step_skewed_rank64_sample(P):
     # the 20K x 200K x 500K shape with a hot first mode (10 ids take half of
-    # the draws), R = 64, at 2M nonzeros: one step against the oracle
-    dims = (20_000, 200_000, 500_000)
-    idx, vals = make_coo(dims, 2_000_000, (("hot", 10, 0.5), ("uniform",), ("uniform",)), "normal", seed=5)
-    facs = make_factors(dims, 64, "normal_over_sqrt_r", seed=5)
-    T, Y, got, lam, fit, start, Yo, lamo, fito = _run_case(P, idx, vals, dims, facs, "f32")
-    tol = 1e-5 * 3 * _kappa_max(start, Yo)
+    # the draws), R = 64, at 2M nonzeros: one FP32 step against the oracle
+    idx, vals = make_coo(SKEWED_DIMS, 2_000_000, SKEWED_LAWS, "normal", seed=5)
+    facs = make_factors(SKEWED_DIMS, 64, "normal_over_sqrt_r", seed=5)
+    T, Y, got, lam, fit, start, Yo, lamo, fito = _run_case(P, idx, vals, SKEWED_DIMS, facs, "f32")
+    assert _kappa_max(start, Yo) <= 50
     for n in range(3):
-        assert rel_fro(got[n], Yo[n]) <= tol, (n, rel_fro(got[n], Yo[n]), tol)
-    assert rel_fro(lam, lamo) <= tol
-    inner = float(lamo @ np.sum(oracle.mttkrp(idx, vals, Yo, 2, dims) * Yo[2], axis=0))
-    assert abs(fit - fito) <= _fit_tol(vals, Yo, lamo, inner, tol) + 1e-12
+        assert rel_fro(got[n], Yo[n]) <= ALS_TOL, (n, rel_fro(got[n], Yo[n]))
+    assert rel_fro(lam, lamo) <= ALS_TOL
+    inner = float(lamo @ np.sum(oracle.mttkrp(idx, vals, Yo, 2, SKEWED_DIMS) * Yo[2], axis=0))
+    assert abs(fit - fito) <= _fit_tol(vals, Yo, lamo, inner, ALS_TOL) + 1e-12
+
+
+def test_als_skewed_bf16_r64_ten_iterations(P):
+    # CP-ALS as the skewed workload runs it (Algorithm 1): BF16 factors, FP32
+    # spMTTKRP accumulation, FP64-accurate Gram matrices and solve, R = 64,
+    # ten iterations from one seeded start, at 2M of its 200M nonzeros.  The
+    # values are N(0, 1) with no low-rank structure, so the fit stays near
+    # 1e-5; fits are compared relative to their size.
+    # (a) iterations 1, 5 and 10 against one oracle step from the GPU's own
+    #     previous iterate: the FP32 spMTTKRP error (~1e-6) flips the BF16
+    #     rounding of a few factor entries by one BF16 step (2^-8 relative),
+    #     so the factors and lambda agree within 1e-2 and the fit within 1e-2
+    #     of its value;
+    # (b) the fit after every iteration against the oracle's own ten
+    #     iterations from the same start, within 2e-2 of its value, and the
+    #     final factors and lambda within 5e-2.
+    idx, vals = make_coo(SKEWED_DIMS, 2_000_000, SKEWED_LAWS, "normal", seed=0)
+    facs = make_factors(SKEWED_DIMS, 64, "normal_over_sqrt_r", seed=0)
+    T = P.FlycooTensor(idx, vals, SKEWED_DIMS)
+    Y = [torch.from_numpy(f).cuda().to(torch.bfloat16).contiguous() for f in facs]
+    start = [to_np(y.float()).astype(np.float64) for y in Y]
+    prev = start
+    fits = []
+    lam = None
+    for it in range(10):
+        lam, fit = T.cp_als_step(Y, lam)
+        fits.append(fit)
+        got = [to_np(y.float()).astype(np.float64) for y in Y]
+        if it in (0, 4, 9):
+            Yo, lamo, fito = cp.cp_als_step(idx, vals, SKEWED_DIMS, prev, store="bf16")
+            for n in range(3):
+                assert rel_fro(got[n], Yo[n]) <= 1e-2, (it, n, rel_fro(got[n], Yo[n]))
+            assert rel_fro(to_np(lam), lamo) <= 1e-2, (it, rel_fro(to_np(lam), lamo))
+            assert abs(fit - fito) <= 1e-2 * abs(fito) + 1e-9, (it, fit, fito)
+        prev = got
+    assert T.layout_mode == 0
+    assert all(b > a for a, b in zip(fits, fits[1:])), fits
+    traj = list(start)
+    for it in range(10):
+        traj, lamo, fito = cp.cp_als_step(idx, vals, SKEWED_DIMS, traj, store="bf16")
+        assert abs(fits[it] - fito) <= 2e-2 * abs(fito) + 1e-9, (it, fits[it], fito)
+    for n in range(3):
+        assert rel_fro(prev[n], traj[n]) <= 5e-2, (n, rel_fro(prev[n], traj[n]))
+    assert rel_fro(to_np(lam), lamo) <= 5e-2
 
 
 def _dense_model(Y, lam):

@@ -1,7 +1,13 @@
 """Full-size parity on the Nell-2-sized workload (12,000 x 9,000 x 29,000,
 77M nonzeros, Zipf(1.1) indices, R = 32) in the launch configuration the
-benchmark times (default partition parameters): sampled output rows against
-the oracle row by row, and layout properties that hold at any size."""
+benchmark times (default partition parameters):
+
+* every output row of every mode against the FP64 oracle, FP32 factors and
+  BF16 factors (the whole matrices, not a sample);
+* the layout the fused remap writes in each pass, bit for bit against the
+  oracle's layout of the next mode;
+* the stage tiles' compute orders: each a permutation of its tile that sorts
+  it stably by output index."""
 import numpy as np
 import pytest
 
@@ -23,68 +29,82 @@ def data():
     import paper_2309_09131_gb300 as P
     idx, vals, facs = make_workload(WL)
     T = P.FlycooTensor(idx, vals, WL.dims)
-    return P, T, idx, vals, facs
+    yield P, T, idx, vals, facs
+    T.close()
+    torch.cuda.empty_cache()
 
 
-def _sample_rows(idx_n, I, rng):
-    counts = np.bincount(idx_n, minlength=I)
-    heavy = np.argsort(counts)[-6:]
-    empty = np.nonzero(counts == 0)[0][:4]
-    rand = rng.choice(I, size=12, replace=False)
-    return np.unique(np.concatenate([heavy, empty, rand, [0, I - 1]])).astype(np.uint32)
-
-
-def test_sampled_rows_fp32_and_bf16(data):
+def test_whole_outputs_fp32_and_bf16(data):
     P, T, idx, vals, facs = data
-    rng = np.random.default_rng(0)
+    N = len(WL.dims)
     Y64 = oracle.factors_f64(facs)
     Yb64 = oracle.factors_f64(facs, bf16=True)
-    rows = [_sample_rows(idx[n], WL.dims[n], rng) for n in range(3)]
-    for dtype in (torch.float32, torch.bfloat16):
+    got = {}
+    for name, dtype in (("f32", torch.float32), ("bf16", torch.bfloat16)):
         Y = [torch.from_numpy(f).cuda().to(dtype) for f in facs]
         outs = T.all_modes(Y)
         torch.cuda.synchronize()
-        for n in range(3):
-            got = to_np(outs[n])[rows[n]]
-            ref = oracle.mttkrp_rows(idx, vals, Y64, n, rows[n], WL.dims)
-            if dtype == torch.float32:
-                assert rel_fro(got, ref) <= 1e-5
-            else:
-                refb = oracle.mttkrp_rows(idx, vals, Yb64, n, rows[n], WL.dims)
-                assert rel_fro(got, refb) <= 1e-5
-                assert rel_fro(got, ref) <= 1e-2
-    assert T.layout_mode == 0
-
-
-def test_layout_properties_full_size(data):
-    P, T, idx, vals, facs = data
-    N = 3
+        assert T.layout_mode == 0
+        got[name] = [to_np(o) for o in outs]
+        del Y, outs
     for n in range(N):
-        if n:
-            T.remap(n)
-        li, lv = T.export_layout()
-        c = to_np(li).view(np.uint32)
-        info = T.info
-        m, tile = info["m"], info["tile"]
-        # super-shards of mode n are contiguous and ascending (ss_n = c_n div m_n)
-        assert np.all(np.diff(c[n].astype(np.int64) // m[n]) >= 0)
-        # every layout tile (tile positions from each shard start) is sorted by c_n
+        ref = oracle.mttkrp(idx, vals, Y64, n, WL.dims)
+        assert rel_fro(got["f32"][n], ref) <= 1e-5, (n, rel_fro(got["f32"][n], ref))
+        assert rel_fro(got["bf16"][n], ref) <= 1e-2, (n, rel_fro(got["bf16"][n], ref))
+        refb = oracle.mttkrp(idx, vals, Yb64, n, WL.dims)
+        assert rel_fro(got["bf16"][n], refb) <= 1e-5, (n, rel_fro(got["bf16"][n], refb))
+
+
+def test_fused_remap_layout_bitexact_full_size(data):
+    P, T, idx, vals, facs = data
+    N = len(WL.dims)
+    info = T.info
+    m = info["m"]
+    if T.layout_mode != 0:
+        T.remap(0)
+    Y = [torch.from_numpy(f).cuda() for f in facs]
+    vals_bits = vals.view(np.uint32)
+    orders = {}
+
+    def order_of(n):
+        if n not in orders:
+            orders[n] = oracle.layout_order(idx, n, m)
+        return orders[n]
+
+    for n in range(N):
+        # the stage tiles' compute orders of L_n: a permutation of each tile,
+        # sorted by c_n with ties in layout order
+        rows = idx[n][order_of(n)].astype(np.int64)
         _, sp, _ = T.export_partition(n)
-        starts = np.concatenate([np.arange(a, b, tile) for a, b in zip(sp[:-1], sp[1:])]).astype(np.int64)
-        tile_id = np.zeros(c.shape[1], dtype=np.int64)
-        tile_id[starts[1:]] = 1
-        tile_id = np.cumsum(tile_id)
-        d = np.diff(c[n].astype(np.int64))
-        assert np.all(d[tile_id[1:] == tile_id[:-1]] >= 0), "a layout tile is not sorted by c_n"
-        if n == 0:
-            # a permutation of the input: same coordinates and values as a multiset
-            key_in = (idx[0].astype(np.int64) * WL.dims[1] + idx[1]) * WL.dims[2] + idx[2]
-            key_out = (c[0].astype(np.int64) * WL.dims[1] + c[1]) * WL.dims[2] + c[2]
-            o_in = np.argsort(key_in)
-            o_out = np.argsort(key_out)
-            np.testing.assert_array_equal(key_in[o_in], key_out[o_out])
-            np.testing.assert_array_equal(vals[o_in], to_np(lv)[o_out])
-    T.remap(0)
+        for stage in (512, 1024):
+            perm = to_np(T.export_tile_order(n, stage)).view(np.uint16).astype(np.int64)
+            starts = np.concatenate([np.arange(a, b, stage) for a, b in zip(sp[:-1], sp[1:])]).astype(np.int64)
+            tid = np.zeros(rows.size, dtype=np.int64)
+            tid[starts[1:]] = 1
+            tid = np.cumsum(tid)
+            ln = np.diff(np.append(starts, rows.size))
+            assert np.all(perm < ln[tid]), stage
+            # a permutation of each tile: sorted within the tile, its local indexes
+            # are exactly 0 .. len-1
+            loc = np.sort(tid * 65536 + perm)
+            np.testing.assert_array_equal(loc, tid * 65536 + (np.arange(rows.size) - starts[tid]))
+            r = rows[starts[tid] + perm]
+            same = tid[1:] == tid[:-1]
+            dr = np.diff(r)
+            assert np.all(dr[same] >= 0), stage
+            assert np.all(np.diff(perm)[same & (dr == 0)] > 0), stage
+            del perm, loc, r
+        # one fused pass of mode n, then the stored layout is L_{n+1} exactly
+        out = torch.empty((WL.dims[n], WL.rank), device="cuda")
+        P.flycoo_spmttkrp(T.h, n, Y, out, (n + 1) % N)
+        torch.cuda.synchronize()
+        nx = (n + 1) % N
+        li, lv = T.export_layout()
+        order = order_of(nx)
+        np.testing.assert_array_equal(to_np(li).view(np.uint32), idx[:, order])
+        np.testing.assert_array_equal(to_np(lv).view(np.uint32), vals_bits[order])
+        assert T.layout_mode == nx
+        del li, lv, out
     info = T.info
     # Section III-A shard count: S_n = sum_j ceil(|SS_n,j| / g)
     for n in range(N):

@@ -43,10 +43,11 @@ def test_adjoint_matches_oracle_and_identity(P, dims, nnz, R, g):
     for mode in range(N):
         G = rng.standard_normal((dims[mode], R)).astype(np.float32)
         grads = [torch.full_like(y, float("nan")) if w != mode else None for w, y in enumerate(Y)]
-        P.flycoo_mttkrp_adjoint(T.h, mode, Y, torch.from_numpy(G).cuda(), grads)
+        gv = torch.full((nnz,), float("nan"), device="cuda")
+        P.flycoo_mttkrp_adjoint(T.h, mode, Y, torch.from_numpy(G).cuda(), grads, gv)
         torch.cuda.synchronize()
         assert T.layout_mode == mode
-        _, dY = cp.mttkrp_adjoint(idx, vals, dims, Y64, mode, G.astype(np.float64), wrt_vals=False)
+        dv, dY = cp.mttkrp_adjoint(idx, vals, dims, Y64, mode, G.astype(np.float64), wrt_vals=True)
         M = oracle.mttkrp(idx, vals, Y64, mode, dims)
         lhs = float(np.sum(G.astype(np.float64) * M))
         for w in range(N):
@@ -56,6 +57,59 @@ def test_adjoint_matches_oracle_and_identity(P, dims, nnz, R, g):
             assert rel_fro(got, dY[w]) <= TOL, (mode, w, rel_fro(got, dY[w]))
             # <G, M_mode(Y)> = <dY_w, Y_w>
             assert abs(float(np.sum(got.astype(np.float64) * Y64[w])) - lhs) <= 1e-5 * abs(lhs) + 1e-6
+        # the value gradient, in input order, and <dvals, vals> = <G, M> (M is linear in the values)
+        gvn = to_np(gv).astype(np.float64)
+        assert rel_fro(gvn, dv) <= TOL, (mode, rel_fro(gvn, dv))
+        assert abs(float(gvn @ vals.astype(np.float64)) - lhs) <= 1e-5 * np.abs(dv) @ np.abs(vals) + 1e-6
+
+
+def test_adjoint_bf16_factors(P):
+    # BF16 factors and a BF16 upstream gradient, FP32 accumulation: within 1e-5
+    # of the oracle on the same BF16 values, within the 1e-2 bar of the FP32 ones
+    dims = (200, 150, 120)
+    nnz, R, mode = 25_000, 32, 1
+    idx, vals = random_coo(dims, nnz, seed=8, law="zipf", value_law="lognormal")
+    facs = make_factors(dims, R, "normal", seed=8)
+    G = np.random.default_rng(8).standard_normal((dims[mode], R)).astype(np.float32)
+    T = P.FlycooTensor(idx, vals, dims, g=512, bins=23)
+    Yb = [y.bfloat16() for y in _fac(facs)]
+    grads = [torch.empty((d, R), device="cuda") if w != mode else None for w, d in enumerate(dims)]
+    gv = torch.empty(nnz, device="cuda")
+    P.flycoo_mttkrp_adjoint(T.h, mode, Yb, torch.from_numpy(G).cuda().bfloat16(), grads, gv)
+    torch.cuda.synchronize()
+    Yb64 = oracle.factors_f64(facs, bf16=True)
+    Gb64 = oracle.factors_f64([G], bf16=True)[0]
+    dvb, dYb = cp.mttkrp_adjoint(idx, vals, dims, Yb64, mode, Gb64, wrt_vals=True)
+    dv, dY = cp.mttkrp_adjoint(idx, vals, dims, oracle.factors_f64(facs), mode, G.astype(np.float64), wrt_vals=True)
+    for w in (0, 2):
+        assert rel_fro(to_np(grads[w]), dYb[w]) <= TOL
+        assert rel_fro(to_np(grads[w]), dY[w]) <= 1e-2
+    assert rel_fro(to_np(gv), dvb) <= TOL
+    assert rel_fro(to_np(gv), dv) <= 1e-2
+
+
+def test_value_gradient_central_differences(P):
+    # L(v) = <G, M_mode(v)>: central differences (eps = 1e-3) of the FP64 oracle
+    # along random unit directions V of the values against <dvals_gpu, V>
+    dims = (60, 50, 40)
+    nnz, R = 6_000, 16
+    idx, vals = random_coo(dims, nnz, seed=9, value_law="normal")
+    facs = make_factors(dims, R, "normal", seed=9)
+    Y64 = oracle.factors_f64(facs)
+    rng = np.random.default_rng(9)
+    T = P.FlycooTensor(idx, vals, dims, g=256, bins=11)
+    for mode in range(3):
+        G = rng.standard_normal((dims[mode], R)).astype(np.float32)
+        gv = torch.empty(nnz, device="cuda")
+        P.flycoo_mttkrp_adjoint(T.h, mode, _fac(facs), torch.from_numpy(G).cuda(), [None] * 3, gv)
+        g64 = to_np(gv).astype(np.float64)
+        eps = 1e-3
+        for _ in range(4):
+            V = rng.standard_normal(nnz)
+            V /= np.linalg.norm(V)
+            Lp = float(np.sum(G * oracle.mttkrp(idx, vals + eps * V, Y64, mode, dims)))
+            Lm = float(np.sum(G * oracle.mttkrp(idx, vals - eps * V, Y64, mode, dims)))
+            assert float(g64 @ V) == pytest.approx((Lp - Lm) / (2 * eps), rel=1e-4, abs=1e-5)
 
 
 def test_spmttkrp_autograd_backward(P):
@@ -64,15 +118,21 @@ def test_spmttkrp_autograd_backward(P):
     facs = make_factors(dims, 16, "normal", seed=4)
     T = P.FlycooTensor(idx, vals, dims, g=512, bins=17)
     Y = [y.clone().requires_grad_(True) for y in _fac(facs)]
+    v = torch.from_numpy(vals).cuda().requires_grad_(True)
     G = torch.randn((dims[1], 16), device="cuda")
-    M = P.spmttkrp(T, 1, Y)
+    M = P.spmttkrp(T, 1, Y, vals=v)
     (M * G).sum().backward()
     assert Y[1].grad is None
     Y64 = oracle.factors_f64(facs)
-    _, dY = cp.mttkrp_adjoint(idx, vals, dims, Y64, 1, to_np(G).astype(np.float64), wrt_vals=False)
+    dv, dY = cp.mttkrp_adjoint(idx, vals, dims, Y64, 1, to_np(G).astype(np.float64), wrt_vals=True)
     for w in (0, 2):
         assert rel_fro(to_np(Y[w].grad), dY[w]) <= TOL
-    np.testing.assert_allclose(to_np(M), oracle.mttkrp(idx, vals, Y64, 1, dims), rtol=1e-4, atol=1e-4)
+    assert rel_fro(to_np(v.grad), dv) <= TOL
+    np.testing.assert_allclose(to_np(M.detach()), oracle.mttkrp(idx, vals, Y64, 1, dims), rtol=1e-4, atol=1e-4)
+    # without values only the factors get gradients; BF16 factors give BF16 gradients
+    Yb = [y.detach().bfloat16().requires_grad_(True) for y in Y]
+    (P.spmttkrp(T, 0, Yb) * torch.randn((dims[0], 16), device="cuda")).sum().backward()
+    assert Yb[0].grad is None and Yb[1].grad.dtype == torch.bfloat16 and Yb[2].grad is not None
 
 
 @pytest.mark.parametrize("dims,nnz,R", [((200, 150, 180), 30_000, 32), ((30, 40, 20, 25), 12_000, 16)])

@@ -47,6 +47,35 @@ LAYOUT_CASES = [
 ]
 
 
+def tile_ids(shard_ptr, stage, nnz):
+    """Stage tile of every position: runs of `stage` positions from each shard
+    start (the last run of a shard shorter).  Returns (tile id, tile start)."""
+    starts = np.concatenate([np.arange(a, b, stage) for a, b in zip(shard_ptr[:-1], shard_ptr[1:])] +
+                            [np.zeros(0)]).astype(np.int64)
+    tid = np.zeros(nnz, dtype=np.int64)
+    tid[starts[1:]] = 1
+    tid = np.cumsum(tid)
+    return tid, starts[tid] if nnz else np.zeros(0, dtype=np.int64)
+
+
+def expected_tile_order(rows, shard_ptr, stage):
+    """The compute order of every stage tile, from its definition: the
+    tile-local indexes of the tile's nonzeros sorted stably by output row."""
+    nnz = rows.size
+    tid, tstart = tile_ids(shard_ptr, stage, nnz)
+    local = np.arange(nnz, dtype=np.int64) - tstart
+    return local[np.lexsort((local, rows, tid))]
+
+
+def check_tile_orders(T, order, rows_of_elem, mode):
+    """Exported compute orders of both stage sizes equal their definition."""
+    _, sp, _ = T.export_partition(mode)
+    rows = rows_of_elem[order]
+    for stage in (512, 1024):
+        got = to_np(T.export_tile_order(mode, stage)).view(np.uint16).astype(np.int64)
+        np.testing.assert_array_equal(got, expected_tile_order(rows, sp.astype(np.int64), stage))
+
+
 @pytest.mark.parametrize("case", LAYOUT_CASES, ids=lambda c: f"{c[0]}-{c[1]}")
 def test_layout_partition_schedule_bitexact(P, case):
     dims, nnz, seed, law, distinct, m, g, bins = case
@@ -55,7 +84,7 @@ def test_layout_partition_schedule_bitexact(P, case):
     info = T.info
     N = len(dims)
     assert info["nnz"] == nnz and info["layout_mode"] == 0
-    ref = oracle.flycoo_layout(idx, dims, info["m"], info["g"], info["bins"], tile=info["tile"])
+    ref = oracle.flycoo_layout(idx, dims, info["m"], info["g"], info["bins"])
     for n in range(N):
         ss, sp, sss = T.export_partition(n)
         np.testing.assert_array_equal(ss, ref[n]["ss_ptr"])
@@ -66,16 +95,26 @@ def test_layout_partition_schedule_bitexact(P, case):
             np.testing.assert_array_equal(bp, ref[n][key][0])
             np.testing.assert_array_equal(items, ref[n][key][1])
         np.testing.assert_array_equal(to_np(T.export_next(n)).view(np.uint32), ref[n]["next"])
-    # the stored tensor walks L_0 -> L_1 -> ... -> L_0 exactly
-    for step in range(N + 1):
-        n = step % N
-        if step:
-            T.remap(n)
+        check_tile_orders(T, ref[n]["order"], idx[n], n)
+
+    def layout_is(n):
         li, lv = T.export_layout()
         order = ref[n]["order"]
         np.testing.assert_array_equal(to_np(li).view(np.uint32), idx[:, order])
         np.testing.assert_array_equal(to_np(lv).view(np.uint32), vals[order].view(np.uint32))
         assert T.layout_mode == n
+
+    layout_is(0)
+    # the standalone remap walks L_0 -> L_1 -> ... -> L_0 exactly
+    for step in range(1, N + 1):
+        T.remap(step % N)
+        layout_is(step % N)
+    # and so does the remap fused into each spMTTKRP pass (Algorithm 2)
+    facs = [torch.randn((d, 16), device="cuda") for d in dims]
+    for n in range(N):
+        T.spmttkrp(n, facs, remap=True)
+        torch.cuda.synchronize()
+        layout_is((n + 1) % N)
 
 
 MTTKRP_CASES = [
@@ -253,3 +292,25 @@ def test_block_cyclic_schedule(P):
     with pytest.raises(P.FlycooError) as e:
         P.FlycooTensor(idx, vals, dims, schedule=7)
     assert e.value.status_name == "FLYCOO_ERR_INVALID_ARG"
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+def test_all_modes_from_host_buffers(P, dtype):
+    # flycoo_all_modes_host: pinned host factors in, host outputs back, the same
+    # kernels in the same order as the device path, so the results are identical
+    dims = (300, 200, 250)
+    idx, vals = random_coo(dims, 40_000, seed=32, law="zipf", value_law="lognormal")
+    facs = make_factors(dims, 32, "normal", seed=32)
+    T = P.FlycooTensor(idx, vals, dims, g=700, bins=29)
+    tdt = torch.bfloat16 if dtype == "bf16" else torch.float32
+    hY = [torch.from_numpy(f).to(tdt).pin_memory() for f in facs]
+    hO = [torch.full((d, 32), float("nan")).pin_memory() for d in dims]
+    T.remap(2)   # the call starts by bringing the tensor back to L_0
+    P.flycoo_all_modes_host(T.h, hY, hO)
+    assert T.layout_mode == 0
+    ref = T.all_modes([y.cuda() for y in hY])
+    for n in range(3):
+        assert torch.equal(hO[n], ref[n].cpu()), n
+    Y64 = oracle.factors_f64(facs, bf16=dtype == "bf16")
+    for n in range(3):
+        assert rel_fro(hO[n].numpy(), oracle.mttkrp(idx, vals, Y64, n, dims)) <= FP32_TOL

@@ -37,18 +37,46 @@ def _plan(P, nnz, ss_ptr, g, bins, schedule=0):
         P.flycoo_plan_destroy(h)
 
 
-def _expected_tiles(shard_ptr, shard_ss, ss_shards, bin_ptr, items, tile):
+def _expected_segments(shard_ss, k, bin_ptr, items):
+    """Segments as the header defines them: maximal runs of shards of one
+    super-shard that follow each other in one bin, numbered by super-shard and
+    then in schedule order.  Returns (segment of each schedule position,
+    seg_ss, ss_seg_ptr)."""
+    tmp, seg_tmp = [], np.zeros(items.size, dtype=np.int64)
+    for b in range(bin_ptr.size - 1):
+        for pos in range(int(bin_ptr[b]), int(bin_ptr[b + 1])):
+            j = int(shard_ss[items[pos]])
+            if pos == bin_ptr[b] or int(shard_ss[items[pos - 1]]) != j:
+                tmp.append(j)
+            seg_tmp[pos] = len(tmp) - 1
+    order = sorted(range(len(tmp)), key=lambda q: (tmp[q], q))
+    renum = np.empty(len(tmp), dtype=np.int64)
+    renum[order] = np.arange(len(tmp))
+    seg_ss = np.array([tmp[q] for q in order], dtype=np.int64)
+    ss_seg_ptr = np.concatenate([[0], np.cumsum(np.bincount(seg_ss, minlength=k))]).astype(np.int64)
+    return seg_tmp, renum, seg_ss, ss_seg_ptr
+
+
+def _expected_tiles(shard_ptr, shard_ss, k, bin_ptr, items, tile):
     """Descriptors as the header defines them: the shards of each bin in
-    schedule order, each cut into runs of `tile` positions."""
+    schedule order, each cut into runs of `tile` positions, flagged at the
+    first and last tile of each segment."""
+    seg_tmp, renum, seg_ss, ss_seg_ptr = _expected_segments(shard_ss, k, bin_ptr, items)
+    nseg = np.diff(ss_seg_ptr)
     desc, tbp = [], [0]
     for b in range(bin_ptr.size - 1):
-        for sh in items[bin_ptr[b]:bin_ptr[b + 1]].tolist():
+        i0, i1 = int(bin_ptr[b]), int(bin_ptr[b + 1])
+        for pos in range(i0, i1):
+            sh = int(items[pos])
             lo, hi = int(shard_ptr[sh]), int(shard_ptr[sh + 1])
             j = int(shard_ss[sh])
+            begin = pos == i0 or seg_tmp[pos - 1] != seg_tmp[pos]
+            end = pos + 1 == i1 or seg_tmp[pos + 1] != seg_tmp[pos]
             for p in range(lo, hi, tile):
                 ln = min(tile, hi - p)
-                flags = (1 if p == lo else 0) | (2 if p + ln == hi else 0) | (4 if ss_shards[j] == 1 else 0)
-                desc += [p, ln | (flags << 16), j, sh]
+                flags = (1 if begin and p == lo else 0) | (2 if end and p + ln == hi else 0) | \
+                        (4 if nseg[j] == 1 else 0)
+                desc += [p, ln | (flags << 16), j, int(renum[seg_tmp[pos]])]
         tbp.append(len(desc) // 4)
     return np.array(desc, dtype=np.uint64), np.array(tbp, dtype=np.uint64)
 
@@ -68,9 +96,16 @@ def _check_against_oracle(P, rows, I, m, g, bins):
     assert np.array_equal(got["ss_bin_ptr"], bp) and np.array_equal(got["ss_items"], it)
     bp, it, _ = oracle.lpt_bins(np.diff(shard_ptr.astype(np.int64)), bins)
     assert np.array_equal(got["shard_bin_ptr"], bp) and np.array_equal(got["shard_items"], it)
-    assert np.array_equal(got["k4_items"], np.nonzero(ss_shards != 1)[0])
+    k = ss_sizes.size
+    _, _, seg_ss, ss_seg_ptr = _expected_segments(shard_ss, k, bp, it)
+    assert np.array_equal(got["seg_ss"], seg_ss)
+    assert np.array_equal(got["ss_seg_ptr"], ss_seg_ptr)
+    assert np.array_equal(got["k4_items"], np.nonzero(np.diff(ss_seg_ptr) != 1)[0])
+    # every shard of a super-shard lies in one of its segments: at most as many
+    # segments as shards, and a super-shard with shards has at least one
+    assert np.all(np.diff(ss_seg_ptr) <= ss_shards) and np.all((np.diff(ss_seg_ptr) > 0) == (ss_shards > 0))
     for z, tile in enumerate(STAGE_TILES):
-        desc, tbp = _expected_tiles(shard_ptr, shard_ss, ss_shards, bp, it, tile)
+        desc, tbp = _expected_tiles(shard_ptr, shard_ss, k, bp, it, tile)
         assert np.array_equal(got[f"tiles_{tile}"], desc), tile
         assert np.array_equal(got[f"tile_bin_ptr_{tile}"], tbp), tile
     return got
@@ -135,6 +170,20 @@ def test_degenerate_plans(P):
     got = _plan(P, 37, [0, 37], 1024, 4)
     assert got["tiles_1024"].tolist() == [0, 37 | (7 << 16), 0, 0]
     assert got["k4_items"].size == 0
+    # one super-shard of three shards in one bin: one segment, so its tiles are
+    # flagged first (shard 0) and last (shard 2) only, and it writes the output
+    got = _plan(P, 3000, [0, 3000], 1024, 1)
+    assert got["seg_ss"].tolist() == [0] and got["k4_items"].size == 0
+    t = got["tiles_1024"].reshape(-1, 4)
+    assert [int(x >> 16) for x in t[:, 1]] == [1 | 4, 4, 2 | 4]
+    assert t[:, 3].tolist() == [0, 0, 0]
+    # the same over two bins: shards 0, 2 in bin 0 and shard 1 in bin 1 form two
+    # segments (numbered bin 0 first), and K4 sums them
+    got = _plan(P, 3000, [0, 3000], 1024, 2)
+    assert got["seg_ss"].tolist() == [0, 0] and got["k4_items"].tolist() == [0]
+    t = got["tiles_1024"].reshape(-1, 4)
+    assert t[:, 0].tolist() == [0, 2048, 1024] and t[:, 3].tolist() == [0, 0, 1]
+    assert [int(x >> 16) for x in t[:, 1]] == [1, 2, 1 | 2]
     # more bins than shards: the extra bins stay empty
     got = _plan(P, 3000, [0, 3000], 1024, 8)
     assert np.diff(got["shard_bin_ptr"].astype(np.int64)).tolist() == [1, 1, 1, 0, 0, 0, 0, 0]

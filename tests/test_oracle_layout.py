@@ -52,6 +52,32 @@ def test_next_layout_is_stable_counting_sort(dims, nnz, seed, widths):
     assert np.array_equal(cur, orders[0])
 
 
+@pytest.mark.parametrize("dims,nnz,seed", CASES + [((70000, 3, 90000), 400, 5)])
+@pytest.mark.parametrize("widths", ["ones", "mixed"])
+def test_layout_order_matches_comparator_sort(dims, nnz, seed, widths):
+    # two codings of the key order: a stable library sort of the key tuple
+    # (packed, or lexsort when the ids need more than 63 bits) and a qsort with
+    # an explicit comparator on (key tuple, input position)
+    idx, _ = random_coo(dims, nnz, seed=seed, distinct=False)
+    N = len(dims)
+    m = [1] * N if widths == "ones" else [max(1, d // 3) for d in dims]
+    for n in range(N):
+        assert np.array_equal(oracle.layout_order(idx, n, m), oracle.layout_order_qsort(idx, n, m))
+
+
+def test_layout_order_wide_keys_use_separate_sort_keys():
+    # 3 modes of ~2^31 ids each need 93 bits: the lexsort branch; its order is
+    # checked against the comparator sort and by direct key comparison
+    rng = np.random.default_rng(9)
+    idx = rng.integers(0, 2**31 - 1, size=(3, 500), dtype=np.int64).astype(np.uint32)
+    idx[:, 100:200] = idx[:, :100]          # exact ties: input order decides
+    for n in range(3):
+        o = oracle.layout_order(idx, n)
+        assert np.array_equal(o, oracle.layout_order_qsort(idx, n))
+        keys = list(zip(idx[n][o].tolist(), idx[(n - 1) % 3][o].tolist(), idx[(n + 1) % 3][o].tolist(), o.tolist()))
+        assert keys == sorted(keys)
+
+
 def test_layout_order_with_unit_widths_sorts_by_coordinates():
     # with m_w = 1 every super-shard id is the coordinate: L_n is ordered by
     # (c_n, c_{n-1}, ..., c_{n+1}) and rows are contiguous
@@ -175,26 +201,3 @@ def test_flycoo_layout_shards_lie_in_their_super_shard():
         assert np.array_equal(np.sort(items), np.arange(sp.size - 1))
         ptr, items = md["ss_bins"]
         assert np.array_equal(np.sort(items), np.arange(md["ss_ptr"].size - 1))
-
-
-@pytest.mark.parametrize("tile", [1, 4, 7, 512])
-def test_stored_order_sorts_tiles_and_keeps_shards(tile):
-    # the stored order only permutes positions inside each layout tile, and each
-    # tile comes out sorted by output coordinate with ties in key order
-    dims = (40, 12, 9)
-    m = [8, 3, 4]
-    idx, _ = random_coo(dims, 500, seed=31, law="zipf", distinct=False)
-    modes = oracle.flycoo_layout(idx, dims, m, 37, 5, tile=tile)
-    for n, md in enumerate(modes):
-        key_order = oracle.layout_order(idx, n, m)
-        sp = md["shard_ptr"].astype(np.int64)
-        pos_in_key = oracle.inverse(key_order)
-        for q in range(sp.size - 1):
-            for a in range(sp[q], sp[q + 1], tile):
-                b = min(a + tile, sp[q + 1])
-                seg = md["order"][a:b]
-                assert sorted(seg.tolist()) == sorted(key_order[a:b].tolist())
-                r = idx[n][seg]
-                assert np.all(np.diff(r.astype(np.int64)) >= 0)
-                same = np.diff(r.astype(np.int64)) == 0
-                assert np.all(np.diff(pos_in_key[seg].astype(np.int64))[same] > 0)

@@ -34,6 +34,9 @@ def test_static_scratch_matches_allocated_scratch(P, dims, nnz, R, dtype, g):
     idx, vals = random_coo(dims, nnz, seed=21, law="zipf", value_law="lognormal")
     facs = [torch.from_numpy(f).cuda().to(dtype) for f in make_factors(dims, R, "normal", seed=21)]
     T = P.FlycooTensor(idx, vals, dims, g=g, bins=48)
+    # every mode has a super-shard split over several segments, so every pass
+    # writes row blocks into the static array and K4 reads them back
+    assert all(k > 0 for k in T.info["fixup_super_shards"])
     ref = T.all_modes(facs)
     ref = [r.clone() for r in ref]
     for call in range(2):
@@ -48,12 +51,45 @@ def test_static_scratch_matches_allocated_scratch(P, dims, nnz, R, dtype, g):
             assert torch.equal(outs[n], ref[n]), (call, n)
 
 
+def test_static_scratch_at_its_size_limit(P):
+    # one 128-row super-shard per mode, 256 equal shards and 256 bins: each bin
+    # holds one shard, so every mode has 256 segments, and at R = 64 their row
+    # blocks fill the 8 MiB array exactly (256 x 128 x 64 x 4 bytes)
+    dims = (128, 128, 128)
+    R = 64
+    idx, vals = random_coo(dims, 256 * 64, seed=22, law="uniform", distinct=False, value_law="normal")
+    facs = [torch.from_numpy(f).cuda() for f in make_factors(dims, R, "normal", seed=22)]
+    T = P.FlycooTensor(idx, vals, dims, g=64, bins=256)
+    info = T.info
+    assert info["segments"] == [256, 256, 256] and info["m"] == [128, 128, 128]
+    ref = [r.clone() for r in T.all_modes(facs)]
+    for call in range(2):
+        outs = [torch.full((d, R), float("nan"), device="cuda") for d in dims]
+        for n in range(3):
+            P.flycoo_spmttkrp_static_scratch(T.h, n, facs, outs[n], (n + 1) % 3)
+        torch.cuda.synchronize()
+        for n in range(3):
+            assert torch.equal(outs[n], ref[n]), (call, n)
+    # one segment more than fits: 257 bins, 257 shards
+    idx, vals = random_coo(dims, 257 * 64, seed=23, law="uniform", distinct=False, value_law="normal")
+    T2 = P.FlycooTensor(idx, vals, dims, g=64, bins=257)
+    assert T2.info["segments"][0] == 257
+    out = torch.empty((128, R), device="cuda")
+    with pytest.raises(P.FlycooError) as e:
+        P.flycoo_spmttkrp_static_scratch(T2.h, 0, facs, out, 1)
+    assert e.value.status_name == "FLYCOO_ERR_INVALID_ARG"
+    assert T2.layout_mode == 0
+
+
 def test_static_scratch_rejects_oversized_requests(P):
-    dims = (50, 40, 30)
+    # mode 0 has 300 super-shards of 128 rows, each split over several bins:
+    # over 256 row blocks of 128 x 64 floats, more than the 8 MiB array holds
+    dims = (38_400, 40, 30)
     idx, vals = random_coo(dims, 20_000, seed=3)
-    T = P.FlycooTensor(idx, vals, dims, g=1, bins=8)   # 20,000 shards per mode
+    T = P.FlycooTensor(idx, vals, dims, g=16, bins=8)
+    assert T.info["segments"][0] > 256
     facs = [torch.randn((d, 64), device="cuda") for d in dims]
-    out = torch.empty((50, 64), device="cuda")
+    out = torch.empty((dims[0], 64), device="cuda")
     with pytest.raises(P.FlycooError) as e:
         P.flycoo_spmttkrp_static_scratch(T.h, 0, facs, out, 1)
     assert e.value.status_name == "FLYCOO_ERR_INVALID_ARG"
