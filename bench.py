@@ -26,12 +26,15 @@ import sys
 import tempfile
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "all-mode spMTTKRP ms & HBM GB/s (% of peak); BF16 vs FP32 at stated err"
 DEFAULT_WORKLOAD = "nell2like_12000x9000x29000_77m_r32"
+PRECISION_WORKLOAD = "delicious4d_1.2mx1.2mx50kx10k_140m_r32"
 FALLBACK_HBM_GBS = 6800.0
 
 
@@ -42,6 +45,8 @@ def parse_args(argv=None):
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["flycoo", "reference"], default="flycoo")
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
+    ap.add_argument("--g", type=int, default=0, help="shard size (0: the library default)")
+    ap.add_argument("--bins", type=int, default=0, help="schedule bins (0: the library default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-bf16", action="store_true")
     ap.add_argument("--no-als", action="store_true")
@@ -49,6 +54,10 @@ def parse_args(argv=None):
     ap.add_argument("--ablations", action="store_true",
                     help="also time passes without the fused remap and the sweep at R = 16, 32, 64")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-precision", action="store_true",
+                    help="skip the FP32-vs-BF16 section on the 4-mode 140M-nonzero tensor")
+    ap.add_argument("--no-oracle-err", action="store_true",
+                    help="skip the per-mode errors against the FP64 oracle on sampled rows")
     ap.add_argument("--cpu-sample", type=int, default=40_000_000, help="nonzeros in the CPU baseline sample")
     args = ap.parse_args(argv)
     if args.warmup < 3:
@@ -169,6 +178,97 @@ def cpu_oracle_pass(idx, vals, facs, dims, sample):
     return sec, b, S
 
 
+def sample_rows(idx_n, I, rng, heavy=64, rand=192):
+    """Rows of one mode for the error against the oracle: the heaviest ones
+    (they carry most of the Frobenius norm) and uniformly random ones."""
+    counts = np.bincount(idx_n, minlength=I)
+    h = np.argsort(counts, kind="stable")[-heavy:]
+    r = rng.choice(I, size=min(rand, I), replace=False)
+    return np.unique(np.concatenate([h, r])).astype(np.uint32)
+
+
+def oracle_row_errors(idx, vals, facs, dims, outs, seed=0):
+    """Relative Frobenius error per mode, on sampled rows, of each named set
+    of GPU outputs against the FP64 oracle on the original FP32 factors.
+    ``outs`` maps a name to N host arrays.  Returns (errors, rows per mode)."""
+    import oracle
+    rng = np.random.default_rng(seed)
+    Y64 = oracle.factors_f64(facs)
+    errs = {k: [] for k in outs}
+    nrows = []
+    for n in range(len(dims)):
+        rows = sample_rows(idx[n], dims[n], rng)
+        ref = oracle.mttkrp_rows(idx, vals, Y64, n, rows, dims)
+        den = float(np.linalg.norm(ref))
+        for k, o in outs.items():
+            d = o[n][rows].astype(np.float64) - ref
+            errs[k].append(float(np.linalg.norm(d)) / den if den else float(np.linalg.norm(d)))
+        nrows.append(int(rows.size))
+    return errs, nrows
+
+
+def _generate_to_dir(name, path):
+    """Child process: draw a named workload and save it as .npy files."""
+    from synth import WORKLOADS, make_workload
+    idx, vals, facs = make_workload(WORKLOADS[name])
+    np.save(os.path.join(path, "idx.npy"), idx)
+    np.save(os.path.join(path, "vals.npy"), vals)
+    for w, f in enumerate(facs):
+        np.save(os.path.join(path, f"f{w}.npy"), f)
+
+
+class BackgroundWorkload:
+    """Draws a workload in a spawned process (started before the first GPU
+    call) while the main benchmark runs; ``get()`` waits and loads it."""
+
+    def __init__(self, name):
+        import multiprocessing as mp
+        self.name = name
+        self.dir = tempfile.mkdtemp(prefix="flycoo_wl_")
+        self.proc = mp.get_context("spawn").Process(target=_generate_to_dir, args=(name, self.dir))
+        self.proc.start()
+
+    def get(self):
+        self.proc.join()
+        if self.proc.exitcode != 0:
+            raise RuntimeError(f"generating {self.name} failed (exit {self.proc.exitcode})")
+        idx = np.load(os.path.join(self.dir, "idx.npy"))
+        vals = np.load(os.path.join(self.dir, "vals.npy"))
+        facs = []
+        w = 0
+        while os.path.exists(os.path.join(self.dir, f"f{w}.npy")):
+            facs.append(np.load(os.path.join(self.dir, f"f{w}.npy")))
+            w += 1
+        self.cleanup()
+        return idx, vals, facs
+
+    def cleanup(self):
+        import shutil
+        if self.proc.is_alive():
+            self.proc.terminate()
+            self.proc.join()
+        shutil.rmtree(self.dir, ignore_errors=True)
+
+
+def time_all_modes(P, T, Y, outs, steps, warmup=3):
+    """Mean all-mode step time (ms) and per-mode times of ``steps`` sweeps."""
+    import torch
+    N = len(Y)
+    for _ in range(warmup):
+        T.all_modes(Y, outs)
+    torch.cuda.synchronize()
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(N + 1)] for _ in range(steps)]
+    for s in range(steps):
+        ev[s][0].record()
+        for n in range(N):
+            P.flycoo_spmttkrp(T.h, n, Y, outs[n], (n + 1) % N)
+            ev[s][n + 1].record()
+    ev[-1][-1].synchronize()
+    total = ev[0][0].elapsed_time(ev[-1][-1]) / steps
+    per_mode = [statistics.mean(ev[s][n].elapsed_time(ev[s][n + 1]) for s in range(steps)) for n in range(N)]
+    return total, per_mode
+
+
 def workload_config(wl):
     """The workload description both arms report (shape, laws, rank, seed)."""
     return {"workload": wl.name, "dims": list(wl.dims), "nnz": wl.nnz, "rank": wl.rank,
@@ -239,10 +339,15 @@ def main(argv=None):
     if args.impl == "reference":
         return run_reference(args)
 
-    import numpy as np
+    rank, local_rank, world = dist_env()
+    # the precision workload is drawn in a spawned process while the main
+    # benchmark runs (started before the first GPU call)
+    bg = None
+    if rank == 0 and world == 1 and not args.no_precision and args.workload == DEFAULT_WORKLOAD:
+        bg = BackgroundWorkload(PRECISION_WORKLOAD)
+
     import torch
 
-    rank, local_rank, world = dist_env()
     torch.cuda.set_device(local_rank)
     if world > 1:
         import torch.distributed as dist
@@ -264,7 +369,7 @@ def main(argv=None):
 
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    T = P.FlycooTensor(idx, vals, wl.dims)
+    T = P.FlycooTensor(idx, vals, wl.dims, g=args.g, bins=args.bins)
     torch.cuda.synchronize()
     create_s = time.perf_counter() - t0
     info = T.info
@@ -340,6 +445,22 @@ def main(argv=None):
         diff = [float(torch.linalg.norm(outs_b[n] - outs[n]) / torch.linalg.norm(outs[n])) for n in range(N)]
         bf16 = {"ms_per_step": ms_b, "gbps": gbps_b,
                 "speedup_vs_f32": step_ms / ms_b, "rel_fro_diff_vs_f32_gpu_per_mode": diff}
+        host_outs = {"f32": [o.cpu().numpy() for o in outs], "bf16": [o.cpu().numpy() for o in outs_b]}
+        del outs_b, Yb
+    else:
+        T.all_modes(Yf, outs)
+        host_outs = {"f32": [o.cpu().numpy() for o in outs]}
+
+    # ---- per-mode error of the timed outputs against the FP64 oracle (sampled rows)
+    oracle_err = None
+    if rank == 0 and not args.no_oracle_err:
+        errs, nrows = oracle_row_errors(idx, vals, facs, wl.dims, host_outs)
+        oracle_err = {"rows_per_mode": nrows, "reference": "FP64 oracle on the FP32 factors",
+                      "rows": "the 64 heaviest rows of each mode and up to 192 uniformly random ones",
+                      **{f"{k}_rel_fro_per_mode": v for k, v in errs.items()}}
+        if bf16 is not None:
+            bf16["rel_fro_err_vs_oracle_per_mode"] = errs["bf16"]
+    del host_outs
 
     # ---- CP-ALS iterations (Algorithm 1 with the least-squares update) on the same tensor
     als = None
@@ -433,35 +554,28 @@ def main(argv=None):
         extra["all_mode_ms_block_cyclic_schedule"] = s0.elapsed_time(s1) / args.steps
         Tb.close()
 
-    # ---- end to end through the public API: pinned host factors in, outputs back out
+    # ---- end to end through the C ABI with host buffers: flycoo_all_modes_host
+    # copies the pinned host factors in, runs the N fused passes and copies
+    # every output back, then waits for the stream
     e2e = None
     if not args.no_e2e:
         hY = [torch.from_numpy(f).pin_memory() for f in facs]
         hO = [torch.empty((d, R), dtype=torch.float32).pin_memory() for d in wl.dims]
-        dY = [torch.empty_like(y) for y in Yf]
         h2d = sum(y.numel() * 4 for y in hY)
         d2h = sum(o.numel() * 4 for o in hO)
         for _ in range(3):
-            for w in range(N):
-                dY[w].copy_(hY[w], non_blocking=True)
-            T.all_modes(dY, outs)
-            for n in range(N):
-                hO[n].copy_(outs[n], non_blocking=True)
+            P.flycoo_all_modes_host(T.h, hY, hO)
         torch.cuda.synchronize()
         barrier()
         se = torch.cuda.Event(enable_timing=True)
         ee = torch.cuda.Event(enable_timing=True)
         se.record()
         for _ in range(args.steps):
-            for w in range(N):
-                dY[w].copy_(hY[w], non_blocking=True)
-            T.all_modes(dY, outs)
-            for n in range(N):
-                hO[n].copy_(outs[n], non_blocking=True)
+            P.flycoo_all_modes_host(T.h, hY, hO)
         ee.record()
         ee.synchronize()
         value_e, ms_e = whole_job_gbps(step_b, se.elapsed_time(ee) / args.steps, world)
-        e2e = {"value": value_e, "unit": "GB/s", "ms_per_step": ms_e,
+        e2e = {"value": value_e, "unit": "GB/s", "ms_per_step": ms_e, "api": "flycoo_all_modes_host",
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
     # ---- CPU baseline: the oracle on a bounded sample (rank 0, single GPU only)
@@ -471,6 +585,40 @@ def main(argv=None):
         cpu = {"value": b / sec / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
                "sample": f"first {S} nonzeros (random COO order) of the workload, all {N} modes, "
                          f"FP64 single-threaded C oracle, {sec:.2f} s"}
+
+    # ---- precision: FP32 against BF16 factor storage on the 4-mode 140M-nonzero
+    # tensor, all modes, each with its per-mode error against the FP64 oracle
+    precision = None
+    if bg is not None:
+        pwl = WORKLOADS[PRECISION_WORKLOAD]
+        t0 = time.perf_counter()
+        pidx, pvals, pfacs = bg.get()
+        wait_s = time.perf_counter() - t0
+        T3 = P.FlycooTensor(pidx, pvals, pwl.dims)
+        info3 = T3.info
+        N3, R3 = len(pwl.dims), pwl.rank
+        o3 = [torch.empty((d, R3), dtype=torch.float32, device="cuda") for d in pwl.dims]
+        psteps = max(5, min(args.steps, 10))
+        sec = {}
+        hout = {}
+        for name, dt, fb in (("f32", torch.float32, 4), ("bf16", torch.bfloat16, 2)):
+            Y3 = [torch.from_numpy(f).cuda().to(dt) for f in pfacs]
+            ms, pm = time_all_modes(P, T3, Y3, o3, psteps)
+            _, b3 = step_bytes(pwl.dims, pwl.nnz, R3, fb, info3["elem_bytes"])
+            hout[name] = [o.cpu().numpy() for o in o3]
+            sec[name] = {"all_mode_ms": ms, "per_mode_ms": pm, "gbps": b3 / (ms * 1e-3) / 1e9,
+                         "frac_of_hbm_peak": b3 / (ms * 1e-3) / 1e9 / hbm_peak()[0], "bytes_per_step": b3}
+            del Y3
+        errs, nrows = oracle_row_errors(pidx, pvals, pfacs, pwl.dims, hout)
+        for name in sec:
+            sec[name]["rel_fro_err_vs_oracle_per_mode"] = errs[name]
+        precision = {"config": {**workload_config(pwl), "g": info3["g"], "bins": info3["bins"],
+                                "elem_bytes": info3["elem_bytes"]},
+                     "steps": psteps, **sec, "bf16_speedup_vs_f32": sec["f32"]["all_mode_ms"] / sec["bf16"]["all_mode_ms"],
+                     "bf16_within_1e-2": all(e <= 1e-2 for e in errs["bf16"]),
+                     "oracle_rows_per_mode": nrows, "generation_wait_s": wait_s}
+        T3.close()
+        del hout, o3
 
     if rank == 0:
         line = {
@@ -484,7 +632,8 @@ def main(argv=None):
                        "parallelism": "replicas" if world > 1 else "single"},
             "all_mode_ms": step_ms, "per_mode_ms": per_mode_ms, "bytes_per_step": step_b,
             "frac_of_hbm_peak": value / world / peak, "bf16": bf16, "preprocess_ms": create_s * 1e3,
-            "generate_s": gen_s, "cp_als": als, "cpopt": cpopt, **extra,
+            "generate_s": gen_s, "oracle_err": oracle_err, "precision": precision,
+            "cp_als": als, "cpopt": cpopt, **extra,
             "memory": {"device_bytes": info["device_bytes"], "tensor_bytes": wl.nnz * elem_bytes,
                        "device_over_tensor": info["device_bytes"] / max(1, wl.nnz * elem_bytes)},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
