@@ -539,6 +539,18 @@ def main(argv=None):
             ranks[str(R2)] = s0.elapsed_time(s1) / args.steps
             del Y2, o2
         extra["all_mode_ms_by_rank_fp32"] = ranks
+        # rank 128 needs super-shards of at most 64 rows: a handle with m = 64,
+        # timed at R = 64 and R = 128 for the comparison
+        T64 = P.FlycooTensor(idx, vals, wl.dims, m=[min(64, d) for d in wl.dims]) if N == 3 else None
+        if T64 is not None:
+            r64 = {}
+            for R2 in (64, 128):
+                Y2 = [torch.from_numpy(f).cuda() for f in make_factors(wl.dims, R2, wl.factor_law, seed=wl.seed)]
+                o2 = [torch.empty((d, R2), dtype=torch.float32, device="cuda") for d in wl.dims]
+                r64[str(R2)] = time_all_modes(P, T64, Y2, o2, args.steps)[0]
+                del Y2, o2
+            extra["all_mode_ms_by_rank_fp32_m64"] = r64
+            T64.close()
         # the same sweep with the block-cyclic schedule instead of Algorithm 3 (LPT)
         Tb = P.FlycooTensor(idx, vals, wl.dims, schedule=P._native.SCHEDULE_BLOCK_CYCLIC)
         for _ in range(2):
@@ -553,6 +565,14 @@ def main(argv=None):
         s1.synchronize()
         extra["all_mode_ms_block_cyclic_schedule"] = s0.elapsed_time(s1) / args.steps
         Tb.close()
+        # the Z-Morton order inside super-shards instead of the key order
+        Tz = P.FlycooTensor(idx, vals, wl.dims, order=P.ORDER_MORTON)
+        zm = {"f32": time_all_modes(P, Tz, Yf, outs, args.steps)[0]}
+        Yz = [y.to(torch.bfloat16) for y in Yf]
+        zm["bf16"] = time_all_modes(P, Tz, Yz, outs, args.steps)[0]
+        extra["all_mode_ms_morton_order"] = zm
+        Tz.close()
+        del Yz
 
     # ---- end to end through the C ABI with host buffers: flycoo_all_modes_host
     # copies the pinned host factors in, runs the N fused passes and copies

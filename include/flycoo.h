@@ -67,14 +67,27 @@ typedef enum {
  *  schedule  FLYCOO_SCHEDULE_LPT (0, default): Algorithm 3 -- items sorted by
  *        size, each to the least-loaded bin; FLYCOO_SCHEDULE_BLOCK_CYCLIC (1):
  *        item i to bin i mod bins, in ascending order (the baseline the paper
- *        compares Algorithm 3 with, Section V-D).  Applies to both schedules. */
+ *        compares Algorithm 3 with, Section V-D).  Applies to both schedules.
+ *  order  FLYCOO_ORDER_KEY (0, default): inside each super-shard of mode n
+ *        the nonzeros follow the other modes' super-shard ids in the order
+ *        n-1, n-2, ..., n+1 (the key order of flycoo_create);
+ *        FLYCOO_ORDER_MORTON (1): they follow the Z-Morton code of the other
+ *        modes' super-shard ids (the Z-Morton ordering of super-shards of the
+ *        preprocessing in Section V-J): bit levels from the most significant
+ *        down, modes n+1, n+2, ..., n-1 at each level, each id with the bit
+ *        width of its mode's largest id; the widths of a mode's other modes
+ *        must add up to at most 64 bits.  Ties keep the input order. */
 #define FLYCOO_SCHEDULE_LPT 0
 #define FLYCOO_SCHEDULE_BLOCK_CYCLIC 1
+#define FLYCOO_ORDER_KEY 0
+#define FLYCOO_ORDER_MORTON 1
 typedef struct {
     uint64_t m[FLYCOO_MAX_MODES];
     uint64_t g;
     uint32_t bins;
     uint32_t schedule;
+    uint32_t order;
+    uint32_t reserved;   /* must be 0 */
 } flycoo_params;
 
 /* Read-only description of a handle. */
@@ -88,6 +101,8 @@ typedef struct {
     uint32_t bins;                              /* schedule bins used                 */
     uint32_t elem_bytes;                        /* bytes of one stored nonzero        */
     uint32_t schedule;                          /* FLYCOO_SCHEDULE_*                  */
+    uint32_t order;                             /* FLYCOO_ORDER_*                     */
+    uint32_t reserved;
     uint64_t super_shards[FLYCOO_MAX_MODES];    /* k_n = ceil(I_n / m_n)              */
     uint64_t shards[FLYCOO_MAX_MODES];          /* S_n = sum_j ceil(|SS_n,j| / g)     */
     uint64_t segments[FLYCOO_MAX_MODES];        /* runs of one super-shard's shards in one bin */
@@ -115,7 +130,10 @@ typedef struct flycoo_tensor *flycoo_handle;
 /*  d_vals  nnz float32 values.  Copied.                                     */
 /*  params  NULL or partition parameters (zeros = defaults).                 */
 /*  out     receives the handle.                                             */
-/* Errors: INVALID_ARG (also m[n] > 128, bins > 2^20, unknown schedule),    */
+/* With params->order = FLYCOO_ORDER_MORTON the order inside each           */
+/* super-shard is the Z-Morton variant described at flycoo_params.           */
+/* Errors: INVALID_ARG (also m[n] > 128, bins > 2^20, unknown schedule or    */
+/* order, Morton codes wider than 64 bits),                                  */
 /* INDEX_RANGE (any coordinate >= its I_w), UNSUPPORTED (N outside 3..5,     */
 /* nnz >= 2^32 - 1), OOM, CUDA.  Waits for `stream`.                         */
 /* ------------------------------------------------------------------------ */
@@ -137,7 +155,10 @@ void flycoo_destroy(flycoo_handle h);
 /*  h_factors  HOST array of N DEVICE pointers, Y_w is I_w x R row-major in  */
 /*             `fdt`, 16-byte aligned.  Entry `mode` is not read (may be     */
 /*             NULL).                                                        */
-/*  R          rank: 16, 32 or 64.                                           */
+/*  R          rank: 16, 32 or 64; or 128 on a 3-mode tensor whose mode     */
+/*             `mode` has super-shards of at most 64 rows (flycoo_params.m:  */
+/*             the m x R FP32 accumulator lives in shared memory), else      */
+/*             UNSUPPORTED.                                                  */
 /*  d_out      I_mode x R FP32, 16-byte aligned, written in full.  It must   */
 /*             not overlap a factor.                                         */
 /*  next_mode  -1: no remap.  (mode + 1) mod N: store every nonzero at its   */
@@ -158,7 +179,8 @@ flycoo_status flycoo_spmttkrp(flycoo_handle h, int mode, const void *const *h_fa
 /* its pass ends; then wait for the stream and check the device error word. */
 /*  h_factors  HOST array of N HOST pointers, Y_w is I_w x R row-major in   */
 /*             `fdt` (pinned memory makes the copies asynchronous)          */
-/*  R          16, 32 or 64                                                 */
+/*  R          16, 32 or 64, or 128 as flycoo_spmttkrp allows it (every    */
+/*             mode then needs m <= 64)                                     */
 /*  h_out      HOST array of N HOST pointers, M_n is I_n x R FP32,          */
 /*             overwritten                                                  */
 /* The first call allocates device staging for the factors and outputs     */

@@ -27,7 +27,8 @@ _LIB_PATH = os.path.join(_HERE, "liboracle.so")
 _lib = None
 
 __all__ = [
-    "build", "mttkrp", "mttkrp_rows", "sampled", "layout_order", "layout_order_qsort", "inverse", "partition",
+    "build", "mttkrp", "mttkrp_rows", "sampled", "layout_order", "layout_order_qsort", "layout_order_morton",
+    "morton_code", "inverse", "partition",
     "lpt", "lpt_bins", "round_bf16", "factors_f64", "flycoo_layout", "remap",
 ]
 
@@ -150,6 +151,41 @@ def sampled(idx, F) -> np.ndarray:
     return out
 
 
+def morton_code(ids: Sequence[np.ndarray], widths: Sequence[int]) -> np.ndarray:
+    """Z-Morton code of id tuples: bit levels from the most significant down;
+    at each level, the bit of every id whose width exceeds the level, in the
+    order the ids are given.  ``widths[t]`` is the bit width of ``ids[t]``.
+    The code is built one bit at a time (at most 64 bits in all)."""
+    assert sum(widths) <= 64
+    n = ids[0].size if ids else 0
+    code = np.zeros(n, dtype=np.uint64)
+    for level in range(max(widths, default=0) - 1, -1, -1):
+        for v, b in zip(ids, widths):
+            if level < b:
+                code = (code << np.uint64(1)) | ((v.astype(np.uint64) >> np.uint64(level)) & np.uint64(1))
+    return code
+
+
+def layout_order_morton(idx, mode: int, m, dims) -> np.ndarray:
+    """pi_n of the Z-Morton variant of L_n (the Z-Morton ordering of
+    super-shards among the preprocessing stages of Section V-J).  Reading:
+    the nonzeros are ordered by the output mode's super-shard id ss_n, then
+    by the Z-Morton code of the other modes' super-shard ids taken in the
+    order n+1, n+2, ..., n-1 (mode indices mod N, each id with the bit width
+    of its mode's largest id, ceil(I_w / m_w) - 1), ties kept in input order."""
+    idx = _coo(idx)
+    N, nnz = idx.shape
+    mm = np.asarray(m, dtype=np.uint64)
+    if nnz == 0:
+        return np.empty(0, dtype=np.uint32)
+    others = [(mode + t) % N for t in range(1, N)]
+    ids = [idx[w].astype(np.uint64) // mm[w] for w in others]
+    widths = [max(1, int((int(dims[w]) + int(mm[w]) - 1) // int(mm[w]) - 1).bit_length()) for w in others]
+    code = morton_code(ids, widths)
+    ssn = idx[mode].astype(np.uint64) // mm[mode]
+    return np.lexsort((code, ssn)).astype(np.uint32)
+
+
 def layout_order(idx, mode: int, m=None) -> np.ndarray:
     """pi_n: position -> original element of layout L_n.
 
@@ -253,11 +289,13 @@ def round_bf16(x: np.ndarray) -> np.ndarray:
     return out
 
 
-def flycoo_layout(idx, dims, m: Sequence[int], g: int, nbins: int) -> List[Dict[str, np.ndarray]]:
+def flycoo_layout(idx, dims, m: Sequence[int], g: int, nbins: int, order: str = "key"
+                  ) -> List[Dict[str, np.ndarray]]:
     """Everything the FLYCOO format fixes for each mode n, from the definitions:
 
     ``order`` (pi_n: the order of L_n, the super-shard key order of
-    ``layout_order``), ``pos`` (its inverse: slot of each element in L_n),
+    ``layout_order``, or with ``order="morton"`` the Z-Morton variant of
+    ``layout_order_morton``), ``pos`` (its inverse: slot of each element in L_n),
     ``ss_ptr`` and ``shard_ptr`` (Section III-A), ``shard_ss`` (super-shard
     of every shard), ``next`` (slot in L_{(n+1) mod N} of the element at each
     position of L_n: the dynamic remap of Section III-B and Algorithm 2),
@@ -269,15 +307,15 @@ def flycoo_layout(idx, dims, m: Sequence[int], g: int, nbins: int) -> List[Dict[
     modes = []
     for n in range(N):
         ss_ptr, shard_ptr = partition(idx[n], int(dims[n]), int(m[n]), int(g))
-        order = layout_order(idx, n, m)
+        order_n = layout_order(idx, n, m) if order == "key" else layout_order_morton(idx, n, m, dims)
         starts = shard_ptr[:-1].astype(np.int64)
         ends = shard_ptr[1:].astype(np.int64)
         ss_sizes = ss_ptr[1:] - ss_ptr[:-1]
         ss_shards = (ss_sizes + np.uint64(g) - np.uint64(1)) // np.uint64(g)
         shard_ss = np.repeat(np.arange(ss_sizes.size, dtype=np.uint32), ss_shards.astype(np.int64))
         modes.append(dict(
-            order=order,
-            pos=inverse(order),
+            order=order_n,
+            pos=inverse(order_n),
             ss_ptr=ss_ptr,
             shard_ptr=shard_ptr,
             shard_ss=shard_ss,

@@ -50,6 +50,8 @@ from ._native import (  # noqa: F401
     PLAN_TILES_1024,
     PLAN_SEG_SS,
     PLAN_SS_SEG_PTR,
+    ORDER_KEY,
+    ORDER_MORTON,
     SCHEDULE_BLOCK_CYCLIC,
     SCHEDULE_LPT,
 )

@@ -35,14 +35,14 @@ class FlycooError(RuntimeError):
 
 class flycoo_params(ctypes.Structure):
     _fields_ = [("m", ctypes.c_uint64 * MAX_MODES), ("g", ctypes.c_uint64), ("bins", ctypes.c_uint32),
-                ("schedule", ctypes.c_uint32)]
+                ("schedule", ctypes.c_uint32), ("order", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
 
 
 class flycoo_info(ctypes.Structure):
     _fields_ = [("N", ctypes.c_int32), ("layout_mode", ctypes.c_int32), ("nnz", ctypes.c_uint64),
                 ("dims", ctypes.c_uint64 * MAX_MODES), ("m", ctypes.c_uint64 * MAX_MODES),
                 ("g", ctypes.c_uint64), ("bins", ctypes.c_uint32), ("elem_bytes", ctypes.c_uint32),
-                ("schedule", ctypes.c_uint32),
+                ("schedule", ctypes.c_uint32), ("order", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
                 ("super_shards", ctypes.c_uint64 * MAX_MODES), ("shards", ctypes.c_uint64 * MAX_MODES),
                 ("segments", ctypes.c_uint64 * MAX_MODES),
                 ("fixup_super_shards", ctypes.c_uint64 * MAX_MODES), ("device_bytes", ctypes.c_uint64)]
@@ -125,16 +125,19 @@ def _dev_ptr(t: torch.Tensor, dtypes, what: str) -> ctypes.c_void_p:
 
 SCHEDULE_LPT = 0
 SCHEDULE_BLOCK_CYCLIC = 1
+ORDER_KEY = 0
+ORDER_MORTON = 1
 
 
 def make_params(m: Optional[Sequence[int]] = None, g: int = 0, bins: int = 0,
-                schedule: int = SCHEDULE_LPT) -> flycoo_params:
+                schedule: int = SCHEDULE_LPT, order: int = ORDER_KEY) -> flycoo_params:
     p = flycoo_params()
     for i, v in enumerate(m or []):
         p.m[i] = int(v)
     p.g = int(g)
     p.bins = int(bins)
     p.schedule = int(schedule)
+    p.order = int(order)
     return p
 
 
@@ -325,7 +328,7 @@ def flycoo_get_info(h) -> dict:
                 super_shards=list(info.super_shards[:N]), shards=list(info.shards[:N]),
                 segments=list(info.segments[:N]),
                 fixup_super_shards=list(info.fixup_super_shards[:N]), device_bytes=info.device_bytes,
-                schedule=info.schedule)
+                schedule=info.schedule, order=info.order)
 
 
 def flycoo_export_layout(h, stream=None):

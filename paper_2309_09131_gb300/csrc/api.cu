@@ -39,10 +39,6 @@ u64 Tensor::device_bytes() const {
     return b;
 }
 
-bool fused_supported(int N, int R, flycoo_dtype dt) {
-    return N >= 3 && N <= 5 && (R == 16 || R == 32 || R == 64) && (dt == FLYCOO_F32 || dt == FLYCOO_BF16);
-}
-
 flycoo_status launch_fused(int N, int R, flycoo_dtype dt, const FusedArgs &a, cudaStream_t s) {
     switch (N) {
     case 3: return launch_fused_n3(R, dt, a, s);
@@ -95,6 +91,25 @@ static flycoo_status upload(DevBuf &d, const std::vector<T> &h, cudaStream_t s) 
     FLY_TRY(d.alloc(std::max<size_t>(h.size() * sizeof(T), 16)));
     if (!h.empty()) FLY_TRY_CUDA(cudaMemcpyAsync(d.p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, s));
     return FLYCOO_OK;
+}
+
+flycoo_status check_pass_rank(const Tensor &t, int mode, int R, const char *who) {
+    if (R == 16 || R == 32 || R == 64) return FLYCOO_OK;
+    if (R == kRank128) {
+        if (t.N != 3) {
+            set_error("%s: rank 128 is built for 3-mode tensors only (this one has %d modes)", who, t.N);
+            return FLYCOO_ERR_UNSUPPORTED;
+        }
+        if (t.mode[mode].m > kMaxRowsAtRank128) {
+            set_error("%s: rank 128 needs super-shards of at most %u rows in mode %d (m = %llu); create the "
+                      "handle with flycoo_params.m[%d] <= %u",
+                      who, kMaxRowsAtRank128, mode, (unsigned long long)t.mode[mode].m, mode, kMaxRowsAtRank128);
+            return FLYCOO_ERR_UNSUPPORTED;
+        }
+        return FLYCOO_OK;
+    }
+    set_error("%s: rank %d not built (16, 32, 64, or 128 on 3-mode tensors)", who, R);
+    return R > 0 ? FLYCOO_ERR_UNSUPPORTED : FLYCOO_ERR_INVALID_ARG;
 }
 
 long long g_alloc_fail_after = -1;
@@ -360,6 +375,15 @@ static flycoo_status create_impl(int N, const uint64_t *h_dims, uint64_t nnz, co
         set_error("flycoo_create: unknown schedule %u", t->schedule);
         return FLYCOO_ERR_INVALID_ARG;
     }
+    if (params && params->reserved != 0) {
+        set_error("flycoo_create: flycoo_params.reserved must be 0");
+        return FLYCOO_ERR_INVALID_ARG;
+    }
+    t->order = params ? params->order : FLYCOO_ORDER_KEY;
+    if (t->order != FLYCOO_ORDER_KEY && t->order != FLYCOO_ORDER_MORTON) {
+        set_error("flycoo_create: unknown order %u", t->order);
+        return FLYCOO_ERR_INVALID_ARG;
+    }
     if (params && params->g) {
         t->g = params->g;
     } else {
@@ -384,7 +408,10 @@ static flycoo_status create_impl(int N, const uint64_t *h_dims, uint64_t nnz, co
     std::vector<std::vector<u32>> ss_ptr;
     FLY_TRY(build_flycoo(*t, d_idx, d_vals, ss_ptr, s));
     for (int n = 0; n < N; ++n) t->max_seg = std::max<u64>(t->max_seg, t->mode[n].nseg());
-    FLY_TRY(t->partials.alloc(std::max<u64>(t->max_seg, 1) * t->max_rows * kMaxRank * sizeof(float)));
+    // one row block per segment, large enough for m x R at every rank the pass is
+    // built for (R <= 64 with m <= 128, R = 128 with m <= 64)
+    const u64 block = std::max<u64>(t->max_rows * kMaxRank, std::min<u64>(t->max_rows, kMaxRowsAtRank128) * kRank128);
+    FLY_TRY(t->partials.alloc(std::max<u64>(t->max_seg, 1) * block * sizeof(float)));
     FLY_TRY(t->loss_part.alloc((size_t)t->bins * sizeof(double)));
     FLY_TRY(t->err.alloc(sizeof(u32)));
     FLY_TRY_CUDA(cudaMemsetAsync(t->err.p, 0, sizeof(u32), s));
@@ -443,10 +470,7 @@ extern "C" flycoo_status flycoo_spmttkrp(flycoo_handle h, int mode, const void *
         set_error("flycoo_spmttkrp: unknown factor dtype %d", (int)fdt);
         return FLYCOO_ERR_INVALID_ARG;
     }
-    if (R != 16 && R != 32 && R != 64) {
-        set_error("flycoo_spmttkrp: rank %d not built (16, 32 or 64)", R);
-        return R > 0 ? FLYCOO_ERR_UNSUPPORTED : FLYCOO_ERR_INVALID_ARG;
-    }
+    FLY_TRY(check_pass_rank(t, mode, R, "flycoo_spmttkrp"));
     if (next_mode != -1 && next_mode != (mode + 1) % t.N) {
         set_error("flycoo_spmttkrp: next_mode must be -1 or (mode+1) mod N = %d", (mode + 1) % t.N);
         return FLYCOO_ERR_INVALID_ARG;
@@ -512,10 +536,7 @@ extern "C" flycoo_status flycoo_all_modes_host(flycoo_handle h, const void *cons
         set_error("flycoo_all_modes_host: unknown factor dtype %d", (int)fdt);
         return FLYCOO_ERR_INVALID_ARG;
     }
-    if (R != 16 && R != 32 && R != 64) {
-        set_error("flycoo_all_modes_host: rank %d not built (16, 32 or 64)", R);
-        return R > 0 ? FLYCOO_ERR_UNSUPPORTED : FLYCOO_ERR_INVALID_ARG;
-    }
+    for (int n = 0; n < t.N; ++n) FLY_TRY(check_pass_rank(t, n, R, "flycoo_all_modes_host"));
     for (int w = 0; w < t.N; ++w)
         if (!h_factors[w] || !h_out[w]) {
             set_error("flycoo_all_modes_host: factor or output %d is NULL", w);
@@ -775,6 +796,7 @@ extern "C" flycoo_status flycoo_get_info(flycoo_handle h, flycoo_info *out) {
     out->bins = t.bins;
     out->elem_bytes = (uint32_t)(t.elem_words * 4);
     out->schedule = t.schedule;
+    out->order = t.order;
     for (int n = 0; n < t.N; ++n) {
         out->dims[n] = t.dims[n];
         out->m[n] = t.mode[n].m;

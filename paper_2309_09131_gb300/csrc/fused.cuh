@@ -51,6 +51,16 @@
 
 namespace flycoo {
 
+// row flushes add to shared memory with red.shared.add (1) or with a load,
+// add and store (0)
+#ifndef FLYCOO_FLUSH_RED
+#define FLYCOO_FLUSH_RED 0
+#endif
+// warps whose groups all have full slices skip the clamps and weights (1)
+#ifndef FLYCOO_FULL_FAST
+#define FLYCOO_FULL_FAST 1
+#endif
+
 // 16-byte loads of one factor row per lane for FP32 factors: a lane takes
 // FLYCOO_FP32_CHUNKS chunks of 4 values, chunk c from the c-th part of the row,
 // so every load instruction of a warp still covers whole sectors.  One chunk is
@@ -65,10 +75,20 @@ namespace flycoo {
 #define FLYCOO_FP32_CHUNKS_R64 2
 #endif
 
+// FP32 factors at R >= 32: each lane loads 32 bytes of a row in one
+// instruction (a group of R/8 lanes covers a row), so a warp's gather serves
+// twice as many nonzeros as with 16-byte loads at the same one line per row
+#ifndef FLYCOO_WIDE_FP32
+#define FLYCOO_WIDE_FP32 1
+#endif
+
 template <int N, int R, bool BF16>
 struct FusedCfg {
-    static constexpr int CV = BF16 ? 8 : 4;         // factor values per 16-byte load
-    static constexpr int CPL = (BF16 || N >= 5) ? 1 : (R >= 64 ? FLYCOO_FP32_CHUNKS_R64 : FLYCOO_FP32_CHUNKS);
+    static constexpr int LB = (!BF16 && FLYCOO_WIDE_FP32 && R >= 32) ? 32 : 16; // bytes per lane load
+    static constexpr int CW = LB / 4;               // 32-bit words per load
+    static constexpr int CV = BF16 ? 2 * CW : CW;   // factor values per load
+    static constexpr int CPL = (LB == 32 || BF16 || N >= 5) ? 1
+                               : (R >= 64 ? FLYCOO_FP32_CHUNKS_R64 : FLYCOO_FP32_CHUNKS);
     static constexpr int VEC = CPL * CV;            // factor values per lane
     static constexpr int L = R / VEC;               // lanes per group
     static constexpr int GPW = 32 / L;              // groups per warp
@@ -78,13 +98,13 @@ struct FusedCfg {
     static constexpr int EW = (N + 1 <= 4) ? 4 : 8; // 32-bit words per stored nonzero
     static constexpr int EQ = EW / 4;               // 16-byte chunks per stored nonzero
     static constexpr int EB = EW * 4;               // bytes per stored nonzero
-    static constexpr int M = (int)kMaxSuperShardRows;
-    // shared memory: two stages (nonzeros, their next slots and the compute
-    // order; the slot and order loads are rounded out to 16-byte boundaries),
-    // the row accumulators and the slice summaries
-    static constexpr size_t NEXT_OFF(size_t cap) { return cap * EB; }
-    static constexpr size_t PERM_OFF(size_t cap) { return cap * EB + (cap + 8) * 4; }
-    static constexpr size_t stage_bytes(size_t cap) { return PERM_OFF(cap) + (cap + 16) * 2; }
+    static constexpr int M = R > kMaxRank ? (int)kMaxRowsAtRank128 : (int)kMaxSuperShardRows; // accumulator rows
+    // shared memory: two stages (nonzeros and the compute order; the order
+    // load is rounded out to 16-byte boundaries, at most cap + 8 entries), the
+    // row accumulators and the slice summaries.  The remap slots are not staged:
+    // they are prefetched into L2 with the tile and read once from there.
+    static constexpr size_t PERM_OFF(size_t cap) { return cap * EB; }
+    static constexpr size_t stage_bytes(size_t cap) { return PERM_OFF(cap) + (cap + 8) * 2; }
     static constexpr size_t ACC = (size_t)M * R * 4;
     static constexpr size_t SUMBUF = (size_t)G * R * 4 + (((size_t)G * 4 + 15) & ~(size_t)15);
     // + 80 bytes: four 16-byte descriptor slots and two mbarriers
@@ -136,6 +156,18 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, u32 parity) {
     return ok != 0;
 }
 
+// bulk prefetch of [src, src + bytes) into L2 (16-byte aligned, a multiple of 16 bytes)
+__device__ __forceinline__ void l2_prefetch_bulk(const void *src, u32 bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
+
+// a streamed 32-bit value read once: not kept in L1, first out of L2
+__device__ __forceinline__ u32 ld_stream_u32(const u32 *p, uint64_t policy) {
+    u32 v;
+    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(policy));
+    return v;
+}
+
 __device__ __forceinline__ void tma_load_1d(void *dst, const void *src, u32 bytes, uint64_t *bar) {
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
                      smem_addr(dst)),
@@ -171,16 +203,37 @@ __device__ __forceinline__ void tma_load_1d_hint(void *dst, const void *src, u32
     tma_load_1d(dst, src, bytes, bar);
 #endif
 }
-__device__ __forceinline__ uint4 ld_factor(const uint4 *p, uint64_t policy) {
+// CW 32-bit words of a factor row, loaded by one lane in one instruction
+template <int CW> struct __align__(CW * 4) Chunk { u32 w[CW]; };
+
+__device__ __forceinline__ Chunk<4> ld_factor(const Chunk<4> *p, uint64_t policy) {
+    Chunk<4> v;
 #if FLYCOO_L2_HINTS
-    uint4 v;
     asm("ld.global.nc.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
-        : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+        : "=r"(v.w[0]), "=r"(v.w[1]), "=r"(v.w[2]), "=r"(v.w[3])
         : "l"(p), "l"(policy));
-    return v;
 #else
-    return __ldg(p);
+    asm("ld.global.nc.v4.u32 {%0, %1, %2, %3}, [%4];"
+        : "=r"(v.w[0]), "=r"(v.w[1]), "=r"(v.w[2]), "=r"(v.w[3])
+        : "l"(p));
 #endif
+    return v;
+}
+
+__device__ __forceinline__ Chunk<8> ld_factor(const Chunk<8> *p, uint64_t policy) {
+    Chunk<8> v;
+#if FLYCOO_L2_HINTS
+    asm("ld.global.nc.L2::cache_hint.v8.u32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8], %9;"
+        : "=r"(v.w[0]), "=r"(v.w[1]), "=r"(v.w[2]), "=r"(v.w[3]), "=r"(v.w[4]), "=r"(v.w[5]), "=r"(v.w[6]),
+          "=r"(v.w[7])
+        : "l"(p), "l"(policy));
+#else
+    asm("ld.global.nc.v8.u32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=r"(v.w[0]), "=r"(v.w[1]), "=r"(v.w[2]), "=r"(v.w[3]), "=r"(v.w[4]), "=r"(v.w[5]), "=r"(v.w[6]),
+          "=r"(v.w[7])
+        : "l"(p));
+#endif
+    return v;
 }
 
 // 16-byte cp.async (global -> shared) for thread 0's look-ahead descriptors:
@@ -202,20 +255,17 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, u32 parity, u32
 }
 
 // ---------------------------------------------------------------------------
-template <bool BF16>
-__device__ __forceinline__ void widen(const uint4 &v, float *f) {
-    if constexpr (BF16) {
-        const u32 w[4] = {v.x, v.y, v.z, v.w};
+// the FP32 values of a chunk: one per word, or two per word for BF16
+template <bool BF16, int CW>
+__device__ __forceinline__ void widen(const Chunk<CW> &v, float *f) {
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            f[2 * q] = __uint_as_float(w[q] << 16);
-            f[2 * q + 1] = __uint_as_float(w[q] & 0xffff0000u);
+    for (int q = 0; q < CW; ++q) {
+        if constexpr (BF16) {
+            f[2 * q] = __uint_as_float(v.w[q] << 16);
+            f[2 * q + 1] = __uint_as_float(v.w[q] & 0xffff0000u);
+        } else {
+            f[q] = __uint_as_float(v.w[q]);
         }
-    } else {
-        f[0] = __uint_as_float(v.x);
-        f[1] = __uint_as_float(v.y);
-        f[2] = __uint_as_float(v.z);
-        f[3] = __uint_as_float(v.w);
     }
 }
 
@@ -231,6 +281,12 @@ __device__ __forceinline__ void st_no_l1(uint4 *p, const uint4 v, uint64_t polic
                  "r"(v.w)
                  : "memory");
 #endif
+}
+
+// shared-memory add without a returned value; used where one thread group is
+// the only writer of the row during the tile, so the order of adds is fixed
+__device__ __forceinline__ void red_shared_add(float *p, float v) {
+    asm volatile("red.shared.add.f32 [%0], %1;" ::"r"(smem_addr(p)), "f"(v) : "memory");
 }
 
 template <int VEC>
@@ -268,19 +324,21 @@ __global__ void __launch_bounds__(256, kBlocksPerSM) fused_mttkrp_remap_kernel(c
     using C = FusedCfg<N, R, BF16>;
     static_assert(!(CPOPT && BF16), "the CP-OPT gradient pass takes FP32 factors");
     constexpr int VEC = C::VEC;     // factor values per lane
-    constexpr int CV = C::CV;       // values per 16-byte load
-    constexpr int CPL = C::CPL;     // 16-byte loads per row per lane
-    constexpr int RV = R / CV;      // 16-byte chunks per factor row
-    constexpr int RC = RV / CPL;    // 16-byte chunks per part of a row (lane k loads chunk k of each part)
+    constexpr int CV = C::CV;       // values per lane load
+    constexpr int CPL = C::CPL;     // loads per row per lane
+    constexpr int RV = R / CV;      // load-sized chunks per factor row
+    constexpr int RC = RV / CPL;    // chunks per part of a row (lane k loads chunk k of each part)
+    using ChunkT = Chunk<C::CW>;
     constexpr int CAP = C::CAP;
     constexpr int G = C::G;
     constexpr int M = C::M;
     constexpr int NF = CPOPT ? N : N - 1;            // factor rows gathered per nonzero
     // nonzeros per group per step: the gathered rows of a step take at most 32
-    // registers per lane (U * NF * CPL 16-byte loads)
-    constexpr int U = (N >= 5 || 8 / (NF * CPL) < 1)
+    // registers per lane (U * NF * CPL loads of CW words)
+    constexpr int LOADREGS = NF * CPL * C::CW;
+    constexpr int U = (N >= 5 || 32 / LOADREGS < 1)
                           ? 1
-                          : ((8 / (NF * CPL)) > FLYCOO_UNROLL3 ? FLYCOO_UNROLL3 : 8 / (NF * CPL));
+                          : ((32 / LOADREGS) > FLYCOO_UNROLL3 ? FLYCOO_UNROLL3 : 32 / LOADREGS);
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float *acc = reinterpret_cast<float *>(smem_raw + 2 * C::STAGE);          // [M][R]
     float *hacc = acc + M * R;                                               // [G][R] head partials
@@ -298,12 +356,12 @@ __global__ void __launch_bounds__(256, kBlocksPerSM) fused_mttkrp_remap_kernel(c
     const bool remap = a.elem_out != nullptr;
     const uint4 *__restrict__ ein = static_cast<const uint4 *>(a.elem_in);
     uint4 *__restrict__ eout = static_cast<uint4 *>(a.elem_out);
-    const uint4 *Yp[N - 1];
+    const ChunkT *Yp[N - 1];
 #pragma unroll
-    for (int t = 0; t < N - 1; ++t) Yp[t] = static_cast<const uint4 *>(a.Y[t]) + k;
+    for (int t = 0; t < N - 1; ++t) Yp[t] = static_cast<const ChunkT *>(a.Y[t]) + k;
     // CP-OPT: the output mode's own factor, for the model value at each nonzero
-    const uint4 *Yo = CPOPT ? static_cast<const uint4 *>(a.Yout) + k : nullptr;
-    double loss = 0.0;
+    const ChunkT *Yo = CPOPT ? static_cast<const ChunkT *>(a.Yout) + k : nullptr;
+    double loss = 0.0;      // CP-OPT: this lane's sum of the tiles' squared residuals
     float *my_hacc = hacc + grp * R;
     // this lane's values of a row: part c holds columns c*(R/CPL) + k*CV .. + CV-1
     auto lane_store = [&](float *row, const float *v) {
@@ -313,6 +371,18 @@ __global__ void __launch_bounds__(256, kBlocksPerSM) fused_mttkrp_remap_kernel(c
     auto lane_add = [&](float *v, const float *row) {
 #pragma unroll
         for (int c = 0; c < CPL; ++c) add_vec<CV>(v + c * CV, row + c * (R / CPL) + k * CV);
+    };
+    // add this lane's values to a row of the accumulator in shared memory
+    auto lane_red = [&](float *row, float *v) {
+#if FLYCOO_FLUSH_RED
+#pragma unroll
+        for (int c = 0; c < CPL; ++c)
+#pragma unroll
+            for (int q = 0; q < CV; ++q) red_shared_add(row + c * (R / CPL) + k * CV + q, v[c * CV + q]);
+#else
+        lane_add(v, row);
+        lane_store(row, v);
+#endif
     };
     const uint64_t pol_stream = l2_policy_evict_first();
     const uint64_t pol_factor = l2_policy_evict_last();
@@ -331,28 +401,27 @@ __global__ void __launch_bounds__(256, kBlocksPerSM) fused_mttkrp_remap_kernel(c
     }
     __syncthreads();
 
-    // thread 0: load a tile (its nonzeros, their next-layout slots and its
-    // compute order) into a stage.  The slot and order arrays are loaded from
-    // the 16-byte boundaries around the tile (both arrays are padded at the
-    // end).  The descriptor written to sdesc reaches the waiting threads
-    // through the release of the arrive and the acquire of their wait on the
-    // same barrier.
+    // thread 0: load a tile (its nonzeros and its compute order) into a stage
+    // and prefetch its next-layout slots into L2.  The order and slot ranges
+    // are rounded out to the 16-byte boundaries around the tile (both arrays
+    // are padded at the end).  The descriptor written to sdesc reaches the
+    // waiting threads through the release of the arrive and the acquire of
+    // their wait on the same barrier.
     auto issue = [&](int st, const uint4 d) {
         const u32 start = d.x, len = d.y & 0xffffu;
         unsigned char *sb = smem_raw + (size_t)st * C::STAGE;
-        const u32 nlo = start & ~3u;
-        const u32 nhi = (start + len + 3u) & ~3u;
         const u32 plo = start & ~7u;
         const u32 phi = (start + len + 7u) & ~7u;
-        u32 bytes = len * C::EB + (phi - plo) * 2u;
-        if (remap) bytes += (nhi - nlo) * 4u;
         sdesc[st] = d;
         fence_proxy_async_smem();
-        mbar_arrive_expect_tx(&bar[st], bytes);
+        mbar_arrive_expect_tx(&bar[st], len * C::EB + (phi - plo) * 2u);
         tma_load_1d_hint(sb, ein + (size_t)start * C::EQ, len * C::EB, &bar[st], pol_stream);
-        if (remap)
-            tma_load_1d_hint(sb + C::NEXT_OFF(CAP), a.next + nlo, (nhi - nlo) * 4u, &bar[st], pol_stream);
         tma_load_1d_hint(sb + C::PERM_OFF(CAP), gperm + plo, (phi - plo) * 2u, &bar[st], pol_stream);
+        if (remap) {
+            const u32 nlo = start & ~3u;
+            const u32 nhi = (start + len + 3u) & ~3u;
+            l2_prefetch_bulk(a.next + nlo, (nhi - nlo) * 4u);
+        }
     };
     if (tid == 0) {
         if (ntile > 0) issue(0, tiles[t_begin]);
@@ -380,17 +449,31 @@ __global__ void __launch_bounds__(256, kBlocksPerSM) fused_mttkrp_remap_kernel(c
         const u32 m_eff = min(a.m, a.I_out - row_base);
         const unsigned char *sb = smem_raw + (size_t)st * C::STAGE;
         const uint4 *selem = reinterpret_cast<const uint4 *>(sb);
-        const u32 *snext = reinterpret_cast<const u32 *>(sb + C::NEXT_OFF(CAP)) + (tstart & 3u);
+        const u32 *gnext = a.next + tstart; // this tile's next-layout slots (prefetched into L2)
         // sperm[p]: tile-local index of the nonzero at compute position p; every
         // read is clamped to the stage, so even the unloaded order of a tile whose
         // wait gave up cannot index outside it
         const uint16_t *sperm = reinterpret_cast<const uint16_t *>(sb + C::PERM_OFF(CAP)) + (tstart & 7u);
         auto elem_at = [&](u32 p) { return min((u32)sperm[p], (u32)CAP - 1u); };
 
-        // 1. remap burst
+        // 1. remap burst: thread i stores the nonzeros i, i + THREADS, ... of the
+        // tile at their slots, loading two slots before each pair of stores
         if (remap && !timed_out) {
-            for (u32 i = tid; i < tlen; i += C::THREADS) {
-                u32 w[C::EW], r[C::EW];
+            constexpr int RPT = (CAP + C::THREADS - 1) / C::THREADS;
+            constexpr int PAIR = RPT >= 2 ? 2 : 1;
+#pragma unroll
+            for (int r0 = 0; r0 < RPT; r0 += PAIR) {
+            u32 dst[PAIR];
+#pragma unroll
+            for (int r = 0; r < PAIR; ++r) {
+                const u32 i = tid + (r0 + r) * C::THREADS;
+                dst[r] = i < tlen ? ld_stream_u32(gnext + i, pol_stream) : 0u;
+            }
+#pragma unroll
+            for (int r = 0; r < PAIR; ++r) {
+                const u32 i = tid + (r0 + r) * C::THREADS;
+                if (i >= tlen) break;
+                u32 w[C::EW], o[C::EW];
 #pragma unroll
                 for (int c = 0; c < C::EQ; ++c) {
                     const uint4 x = selem[i * C::EQ + c];
@@ -400,12 +483,12 @@ __global__ void __launch_bounds__(256, kBlocksPerSM) fused_mttkrp_remap_kernel(c
                     w[4 * c + 3] = x.w;
                 }
 #pragma unroll
-                for (int t = 0; t < C::EW; ++t) r[t] = (t < N) ? w[(t + 1) % N] : w[t];
-                const size_t dst = snext[i];
+                for (int t = 0; t < C::EW; ++t) o[t] = (t < N) ? w[(t + 1) % N] : w[t];
 #pragma unroll
                 for (int c = 0; c < C::EQ; ++c)
-                    st_no_l1(eout + dst * C::EQ + c, make_uint4(r[4 * c], r[4 * c + 1], r[4 * c + 2], r[4 * c + 3]),
-                             pol_stream);
+                    st_no_l1(eout + (size_t)dst[r] * C::EQ + c,
+                             make_uint4(o[4 * c], o[4 * c + 1], o[4 * c + 2], o[4 * c + 3]), pol_stream);
+            }
             }
         }
 
@@ -415,7 +498,8 @@ __global__ void __launch_bounds__(256, kBlocksPerSM) fused_mttkrp_remap_kernel(c
         // run of one row that lies inside the slice is added by this group
         // alone; a run that crosses a slice edge is summed in step 3.
         // (a full tile, the common case, takes the compile-time values)
-        constexpr u32 kChunkFull = ((u32)(CAP + G - 1) / G) | 1u;
+        // (exactly CAP / G when that splits into whole steps; else odd)
+        constexpr u32 kChunkFull = ((u32)CAP % (u32)(G * U) == 0) ? (u32)CAP / G : (((u32)(CAP + G - 1) / G) | 1u);
         constexpr u32 kGeffFull = ((u32)CAP + kChunkFull - 1) / kChunkFull;
         const u32 chunk = (tlen == (u32)CAP) ? kChunkFull : (((tlen + G - 1) / G) | 1u);
         const u32 geff = (tlen == (u32)CAP) ? kGeffFull : (tlen + chunk - 1) / chunk;
@@ -437,16 +521,21 @@ __global__ void __launch_bounds__(256, kBlocksPerSM) fused_mttkrp_remap_kernel(c
         float racc[VEC];
 #pragma unroll
         for (int v = 0; v < VEC; ++v) racc[v] = 0.f;
+        // CP-OPT: squared residuals of this slice (at most a few dozen terms) in
+        // FP32, added to the lane's FP64 sum once per tile
+        float tloss = 0.f;
         u32 crow = min(row_at(min(lo, last)) - row_base, (u32)M - 1u);
         // the first run goes to the head slot when it continues the previous slice's row
         bool first_run = head_shared;
-        auto steps = [&](u32 j0, auto count) {
+        // FULL: every position of the step lies inside the slice (no clamp, weight val)
+        auto steps = [&](u32 j0, auto count, auto full) {
             constexpr int UU = decltype(count)::value;
+            constexpr bool FULL = decltype(full)::value;
             u32 w[UU][N + 1];
-            uint4 y[UU][NF][CPL];
+            ChunkT y[UU][NF][CPL];
 #pragma unroll
             for (int u = 0; u < UU; ++u) {
-                const u32 e = elem_at(min(lo + j0 + u, last));
+                const u32 e = elem_at(FULL ? lo + j0 + u : min(lo + j0 + u, last));
 #pragma unroll
                 for (int c = 0; c < C::EQ; ++c) {
                     const uint4 x = selem[(size_t)e * C::EQ + c];
@@ -469,7 +558,7 @@ __global__ void __launch_bounds__(256, kBlocksPerSM) fused_mttkrp_remap_kernel(c
             }
 #pragma unroll
             for (int u = 0; u < UU; ++u) {
-                const bool valid = lo + j0 + u < hi;
+                const bool valid = FULL || lo + j0 + u < hi;
                 const u32 row = min(w[u][0] - row_base, (u32)M - 1u);
                 float prod[VEC];
 #pragma unroll
@@ -495,7 +584,7 @@ __global__ void __launch_bounds__(256, kBlocksPerSM) fused_mttkrp_remap_kernel(c
 #pragma unroll
                     for (int off = C::L / 2; off >= 1; off >>= 1) mpart += __shfl_xor_sync(0xffffffffu, mpart, off);
                     const float e = val - mpart; // residual x - m
-                    if (valid && k == 0) loss += (double)e * (double)e;
+                    if (valid) tloss = fmaf(e, e, tloss);
                     coef = valid ? -e : 0.f;     // dL/dY_n += -e * prod
                 }
                 if (row != crow) {
@@ -505,9 +594,7 @@ __global__ void __launch_bounds__(256, kBlocksPerSM) fused_mttkrp_remap_kernel(c
                         first_run = false;
                     } else {
                         // a whole row of this tile: only this group holds it
-                        float *dst = acc + crow * R;
-                        lane_add(racc, dst);
-                        lane_store(dst, racc);
+                        lane_red(acc + crow * R, racc);
                     }
                     crow = row;
 #pragma unroll
@@ -518,9 +605,22 @@ __global__ void __launch_bounds__(256, kBlocksPerSM) fused_mttkrp_remap_kernel(c
             }
         };
         if (!timed_out) {
+            using One = std::integral_constant<int, 1>;
+            using Many = std::integral_constant<int, U>;
+            using Yes = std::true_type;
+            using No = std::false_type;
             u32 j0 = 0;
-            for (; j0 + U <= wlen; j0 += U) steps(j0, std::integral_constant<int, U>{});
-            for (; j0 < wlen; ++j0) steps(j0, std::integral_constant<int, 1>{});
+            // warp-uniform: every group of the warp has a full slice of whole steps
+            if (FLYCOO_FULL_FAST && __all_sync(0xffffffffu, hi - lo == wlen && wlen % U == 0)) {
+                for (; j0 < wlen; j0 += U) steps(j0, Many{}, Yes{});
+            } else {
+                for (; j0 + U <= wlen; j0 += U) steps(j0, Many{}, No{});
+                for (; j0 < wlen; ++j0) steps(j0, One{}, No{});
+            }
+        }
+        if constexpr (CPOPT) {
+            // every lane of a group holds the group's residuals: one lane counts them
+            if (k == 0) loss += (double)tloss;
         }
         // the slice's last run: added here when it ends at the slice end, else kept
         // for step 3 (in registers when its row starts in this slice, in the head
@@ -538,9 +638,7 @@ __global__ void __launch_bounds__(256, kBlocksPerSM) fused_mttkrp_remap_kernel(c
                 lane_store(my_hacc, racc);
                 if (k == 0) pass[grp] = 0u;
             } else {
-                float *dst = acc + crow * R;
-                lane_add(racc, dst);
-                lane_store(dst, racc);
+                lane_red(acc + crow * R, racc);
             }
         }
         // one barrier reports both: every lane of a warp that gave up counts (32 per
@@ -675,9 +773,12 @@ flycoo_status launch_fused_dispatch(int R, flycoo_dtype dt, const FusedArgs &a, 
     case 16: return bf ? launch_fused_t<N, 16, true>(a, s) : launch_fused_t<N, 16, false>(a, s);
     case 32: return bf ? launch_fused_t<N, 32, true>(a, s) : launch_fused_t<N, 32, false>(a, s);
     case 64: return bf ? launch_fused_t<N, 64, true>(a, s) : launch_fused_t<N, 64, false>(a, s);
+    case 128:
+        if constexpr (N == 3) return bf ? launch_fused_t<N, 128, true>(a, s) : launch_fused_t<N, 128, false>(a, s);
+        break;
     default: break;
     }
-    set_error("rank %d not built (16, 32 or 64)", R);
+    set_error("rank %d not built for %d modes", R, N);
     return FLYCOO_ERR_UNSUPPORTED;
 }
 

@@ -103,6 +103,12 @@ struct DeviceGuard {
     }
 };
 
+// The ranks a fused spMTTKRP pass of `mode` is built for: 16, 32, 64, and 128
+// on 3-mode tensors whose output mode has super-shards of at most 64 rows.
+// Defined in api.cu.
+struct Tensor;
+flycoo_status check_pass_rank(const Tensor &t, int mode, int R, const char *who);
+
 // --------------------------------------------------------------------------
 // FLYCOO description of one mode (Section III-A)
 // --------------------------------------------------------------------------
@@ -171,6 +177,7 @@ struct Tensor {
     u64 g = 0;
     u32 bins = 0;
     u32 schedule = 0;   // FLYCOO_SCHEDULE_*
+    u32 order = 0;      // FLYCOO_ORDER_*: key order or Z-Morton inside super-shards
     int layout = 0;     // current layout mode
     int elem_words = 4; // 32-bit words per stored nonzero
     int cur = 0;        // which element buffer holds the current layout
@@ -197,7 +204,12 @@ struct Tensor {
     u64 device_bytes() const;
 };
 
-constexpr int kMaxRank = 64;
+constexpr int kMaxRank = 64;   // largest rank of CP-ALS, CP-OPT and the adjoint
+// the spMTTKRP pass is also built for rank 128 on 3-mode tensors; its
+// accumulator then holds super-shards of at most 64 rows (m x R FP32 in
+// shared memory either way)
+constexpr int kRank128 = 128;
+constexpr u32 kMaxRowsAtRank128 = 64;
 // largest super-shard width m_n: the fused kernel keeps a super-shard's output
 // rows (m_n x R FP32) in shared memory
 constexpr u32 kMaxSuperShardRows = 128;
@@ -305,7 +317,6 @@ flycoo_status launch_fixup(int R, const FixupArgs &a, cudaStream_t s);
 // tensor must be in L_0 (grad.cu)
 flycoo_status launch_value_grad(const Tensor &t, int mode, const void *const *Y, const void *G, flycoo_dtype fdt,
                                 int R, float *d_gvals, cudaStream_t s);
-bool fused_supported(int N, int R, flycoo_dtype dt);
 
 // launchers implemented per mode count (fused_n3.cu, fused_n4.cu, fused_n5.cu)
 flycoo_status launch_fused_n3(int R, flycoo_dtype dt, const FusedArgs &a, cudaStream_t s);

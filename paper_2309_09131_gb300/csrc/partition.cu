@@ -254,6 +254,24 @@ __global__ void gather_div_kernel(const u32 *src, const u32 *perm, u32 *dst, u64
         dst[i] = src[perm[i]] / m;
 }
 
+// Z-Morton code of the other modes' super-shard ids of element perm[i], for
+// output mode `mode`: bit levels from the most significant down, modes
+// mode+1, ..., mode-1 at each level, the id of mode w taking width[w] bits;
+// word 0 = the low 32 bits of the code, word 1 = the high 32 bits
+__global__ void morton_key_kernel(const u32 *idx, u64 nnz, int N, int mode, Dims m, Dims width, int maxw,
+                                  const u32 *perm, u32 *keys, int word) {
+    for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < nnz; i += (u64)gridDim.x * blockDim.x) {
+        const u32 e = perm[i];
+        u64 code = 0;
+        for (int level = maxw - 1; level >= 0; --level)
+            for (int t = 1; t < N; ++t) {
+                const int w = (mode + t) % N;
+                if (level < (int)width.d[w]) code = (code << 1) | ((idx[(u64)w * nnz + e] / m.d[w] >> level) & 1u);
+            }
+        keys[i] = word ? (u32)(code >> 32) : (u32)code;
+    }
+}
+
 __global__ void inverse_kernel(const u32 *perm, u32 *inv, u64 n) {
     for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (u64)gridDim.x * blockDim.x)
         inv[perm[i]] = (u32)i;
@@ -406,6 +424,22 @@ flycoo_status build_flycoo(Tensor &t, const u32 *d_idx, const float *d_vals,
     const int N = t.N;
     const u64 nnz = t.nnz;
     ss_ptr_host.assign(N, {});
+    if (t.order == FLYCOO_ORDER_MORTON) {
+        for (int n = 0; n < N; ++n) {
+            int total = 0;
+            for (int q = 1; q < N; ++q) {
+                const int w = (n + q) % N;
+                const u64 kw = (t.dims[w] + t.mode[w].m - 1) / t.mode[w].m;
+                int b = 0;
+                while (b < 32 && (1ull << b) <= kw - 1) ++b;
+                total += std::max(b, 1);
+            }
+            if (total > 64) {
+                set_error("flycoo_create: the Z-Morton code of mode %d needs %d bits (at most 64)", n, total);
+                return FLYCOO_ERR_INVALID_ARG;
+            }
+        }
+    }
     // 1. coordinate range check
     DevBuf err;
     FLY_TRY(err.alloc(sizeof(u32)));
@@ -459,12 +493,41 @@ flycoo_status build_flycoo(Tensor &t, const u32 *d_idx, const float *d_vals,
         FLY_TRY_CUDA(cudaGetLastError());
         return FLYCOO_OK;
     };
-    for (int w = 1; w < N; ++w) FLY_TRY(sort_by_mode(w));
-    FLY_TRY(sort_by_mode(0));
-    FLY_TRY(finish_mode(0));
-    for (int n = 1; n < N; ++n) {
-        FLY_TRY(sort_by_mode(n));
-        FLY_TRY(finish_mode(n));
+    if (t.order == FLYCOO_ORDER_KEY) {
+        for (int w = 1; w < N; ++w) FLY_TRY(sort_by_mode(w));
+        FLY_TRY(sort_by_mode(0));
+        FLY_TRY(finish_mode(0));
+        for (int n = 1; n < N; ++n) {
+            FLY_TRY(sort_by_mode(n));
+            FLY_TRY(finish_mode(n));
+        }
+    } else {
+        // Z-Morton variant: each layout on its own, from the input order, by
+        // stable sorts on the code's low word, its high word, then ss_n
+        Dims mw{}, width{};
+        for (int w = 0; w < N; ++w) {
+            mw.d[w] = (u32)t.mode[w].m;
+            int b = 0;
+            while (b < 32 && (1ull << b) <= kss[w] - 1) ++b;
+            width.d[w] = (u32)std::max(b, 1);
+        }
+        for (int n = 0; n < N; ++n) {
+            int total = 0, maxw = 0;
+            for (int q = 1; q < N; ++q) {
+                total += (int)width.d[(n + q) % N];
+                maxw = std::max(maxw, (int)width.d[(n + q) % N]);
+            }
+            if (nnz) iota_kernel<<<grid, 256, 0, s>>>(vals, nnz);
+            for (int word = 0; word < 2 && word * 32 < total; ++word) {
+                if (nnz)
+                    morton_key_kernel<<<grid, 256, 0, s>>>(d_idx, nnz, N, n, mw, width, maxw, vals, keys, word);
+                FLY_TRY_CUDA(cudaGetLastError());
+                FLY_TRY(stable_sort_pairs(&keys, &vals, &ktmp, &vtmp, b_counts.as<u32>(), b_scan.as<u32>(), nnz,
+                                          std::min(32, total - 32 * word), s));
+            }
+            FLY_TRY(sort_by_mode(n));
+            FLY_TRY(finish_mode(n));
+        }
     }
 
     // 3. host: super-shard pointers -> shards, tiles, schedules (Section III-A, Algorithm 3)

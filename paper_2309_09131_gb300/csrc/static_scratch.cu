@@ -78,10 +78,7 @@ extern "C" flycoo_status flycoo_spmttkrp_static_scratch(flycoo_handle h, int mod
         set_error("flycoo_spmttkrp_static_scratch: unknown factor dtype %d", (int)fdt);
         return FLYCOO_ERR_INVALID_ARG;
     }
-    if (R != 16 && R != 32 && R != 64) {
-        set_error("flycoo_spmttkrp_static_scratch: rank %d not built (16, 32 or 64)", R);
-        return R > 0 ? FLYCOO_ERR_UNSUPPORTED : FLYCOO_ERR_INVALID_ARG;
-    }
+    FLY_TRY(check_pass_rank(t, mode, R, "flycoo_spmttkrp_static_scratch"));
     if (next_mode != -1 && next_mode != (mode + 1) % t.N) {
         set_error("flycoo_spmttkrp_static_scratch: next_mode must be -1 or (mode+1) mod N = %d",
                   (mode + 1) % t.N);

@@ -28,11 +28,12 @@ class FlycooTensor:
     [nnz] float32, ``dims``: mode sizes.  ``m``, ``g``, ``bins`` are the
     partition parameters of ``flycoo_params`` (0 = default); ``schedule``
     is ``SCHEDULE_LPT`` (Algorithm 3, the default) or
-    ``SCHEDULE_BLOCK_CYCLIC``.
+    ``SCHEDULE_BLOCK_CYCLIC``; ``order`` is ``ORDER_KEY`` (the default) or
+    ``ORDER_MORTON`` (Z-Morton order inside the super-shards).
     """
 
     def __init__(self, idx, vals, dims: Sequence[int], m: Optional[Sequence[int]] = None, g: int = 0,
-                 bins: int = 0, stream=None, schedule: int = 0):
+                 bins: int = 0, stream=None, schedule: int = 0, order: int = 0):
         idx_t = _as_cuda(idx, torch.int32)
         vals_t = _as_cuda(vals, torch.float32)
         self.N = int(idx_t.shape[0])
@@ -40,7 +41,7 @@ class FlycooTensor:
         self.dims = [int(d) for d in dims]
         self.h = None
         self.h = nat.flycoo_create(self.N, self.dims, self.nnz, idx_t, vals_t,
-                                   nat.make_params(m, g, bins, schedule), stream)
+                                   nat.make_params(m, g, bins, schedule, order), stream)
 
     def close(self):
         if self.h:

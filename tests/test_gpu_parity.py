@@ -76,15 +76,17 @@ def check_tile_orders(T, order, rows_of_elem, mode):
         np.testing.assert_array_equal(got, expected_tile_order(rows, sp.astype(np.int64), stage))
 
 
+@pytest.mark.parametrize("order", ["key", "morton"])
 @pytest.mark.parametrize("case", LAYOUT_CASES, ids=lambda c: f"{c[0]}-{c[1]}")
-def test_layout_partition_schedule_bitexact(P, case):
+def test_layout_partition_schedule_bitexact(P, case, order):
     dims, nnz, seed, law, distinct, m, g, bins = case
     idx, vals = random_coo(dims, nnz, seed=seed, law=law, distinct=distinct)
-    T = P.FlycooTensor(idx, vals, dims, m=m, g=g, bins=bins)
+    T = P.FlycooTensor(idx, vals, dims, m=m, g=g, bins=bins,
+                       order=P.ORDER_MORTON if order == "morton" else P.ORDER_KEY)
     info = T.info
     N = len(dims)
-    assert info["nnz"] == nnz and info["layout_mode"] == 0
-    ref = oracle.flycoo_layout(idx, dims, info["m"], info["g"], info["bins"])
+    assert info["nnz"] == nnz and info["layout_mode"] == 0 and info["order"] == (order == "morton")
+    ref = oracle.flycoo_layout(idx, dims, info["m"], info["g"], info["bins"], order=order)
     for n in range(N):
         ss, sp, sss = T.export_partition(n)
         np.testing.assert_array_equal(ss, ref[n]["ss_ptr"])
@@ -314,3 +316,75 @@ def test_all_modes_from_host_buffers(P, dtype):
     Y64 = oracle.factors_f64(facs, bf16=dtype == "bf16")
     for n in range(3):
         assert rel_fro(hO[n].numpy(), oracle.mttkrp(idx, vals, Y64, n, dims)) <= FP32_TOL
+
+
+@pytest.mark.parametrize("dims,nnz,law,m,g,bins", [
+    ((1000, 800, 600), 100_000, "uniform", (64, 64, 64), 0, 0),
+    ((5000, 3000, 2000), 80_000, "zipf", (64, 32, 64), 2048, 50),
+    ((200, 150, 40), 30_000, "zipf", (50, 64, 40), 333, 37),
+])
+def test_rank128_all_modes(P, dims, nnz, law, m, g, bins):
+    # rank 128 on 3-mode tensors whose super-shards have at most 64 rows
+    idx, vals = random_coo(dims, nnz, seed=12, law=law, distinct=True, value_law="lognormal")
+    facs = make_factors(dims, 128, "normal", seed=12)
+    T = P.FlycooTensor(idx, vals, dims, m=m, g=g, bins=bins)
+    Y64 = oracle.factors_f64(facs)
+    Yb64 = oracle.factors_f64(facs, bf16=True)
+    for dtype in (torch.float32, torch.bfloat16):
+        outs = T.all_modes(_cuda_factors(facs, dtype))
+        torch.cuda.synchronize()
+        assert T.layout_mode == 0
+        for n in range(3):
+            ref = oracle.mttkrp(idx, vals, Yb64 if dtype == torch.bfloat16 else Y64, n, dims)
+            assert rel_fro(to_np(outs[n]), ref) <= FP32_TOL, (dtype, n, rel_fro(to_np(outs[n]), ref))
+
+
+def test_rank128_needs_narrow_super_shards_and_three_modes(P):
+    dims = (300, 200, 100)
+    idx, vals = random_coo(dims, 5_000, seed=13)
+    facs = [torch.randn((d, 128), device="cuda") for d in dims]
+    out = torch.empty((300, 128), device="cuda")
+    T = P.FlycooTensor(idx, vals, dims)          # default m = 128
+    with pytest.raises(P.FlycooError) as e:
+        P.flycoo_spmttkrp(T.h, 0, facs, out, 1)
+    assert e.value.status_name == "FLYCOO_ERR_UNSUPPORTED" and "m[0] <= 64" in str(e.value)
+    assert T.layout_mode == 0
+    dims4 = (30, 20, 10, 8)
+    idx4, vals4 = random_coo(dims4, 2_000, seed=14)
+    T4 = P.FlycooTensor(idx4, vals4, dims4, m=(16, 16, 8, 8))
+    f4 = [torch.randn((d, 128), device="cuda") for d in dims4]
+    with pytest.raises(P.FlycooError) as e:
+        P.flycoo_spmttkrp(T4.h, 0, f4, torch.empty((30, 128), device="cuda"), 1)
+    assert e.value.status_name == "FLYCOO_ERR_UNSUPPORTED" and "3-mode" in str(e.value)
+    # the handle stays usable at a built rank
+    T.all_modes([f[:, :64].contiguous() for f in facs])
+    torch.cuda.synchronize()
+
+
+@pytest.mark.parametrize("case", MTTKRP_CASES[1:5], ids=lambda c: f"{c[0]}-{c[1]}-R{c[3]}")
+def test_all_modes_morton_order(P, case):
+    # the Z-Morton variant changes the order inside super-shards, never the result
+    dims, nnz, law, R, g, bins = case
+    N = len(dims)
+    idx, vals = random_coo(dims, nnz, seed=11, law=law, distinct=True, value_law="lognormal")
+    facs = make_factors(dims, R, "normal", seed=11)
+    T = P.FlycooTensor(idx, vals, dims, g=g, bins=bins, order=P.ORDER_MORTON)
+    outs = T.all_modes(_cuda_factors(facs, torch.float32))
+    torch.cuda.synchronize()
+    assert T.layout_mode == 0
+    Y64 = oracle.factors_f64(facs)
+    for n in range(N):
+        assert rel_fro(to_np(outs[n]), oracle.mttkrp(idx, vals, Y64, n, dims)) <= FP32_TOL
+
+
+def test_morton_code_width_limit(P):
+    # 3 other modes of 2^22 super-shards each need 66 bits: refused at create
+    dims = (4, 1 << 29, 1 << 29, 1 << 29)
+    idx = np.zeros((4, 10), dtype=np.uint32)
+    vals = np.ones(10, dtype=np.float32)
+    with pytest.raises(P.FlycooError) as e:
+        P.FlycooTensor(idx, vals, dims, order=P.ORDER_MORTON)
+    assert e.value.status_name == "FLYCOO_ERR_INVALID_ARG" and "64" in str(e.value)
+    with pytest.raises(P.FlycooError) as e:
+        P.FlycooTensor(idx, vals, (4, 4, 4, 4), order=7)
+    assert e.value.status_name == "FLYCOO_ERR_INVALID_ARG"

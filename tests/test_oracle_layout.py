@@ -201,3 +201,63 @@ def test_flycoo_layout_shards_lie_in_their_super_shard():
         assert np.array_equal(np.sort(items), np.arange(sp.size - 1))
         ptr, items = md["ss_bins"]
         assert np.array_equal(np.sort(items), np.arange(md["ss_ptr"].size - 1))
+
+
+def test_morton_code_hand_worked():
+    g = {"pairs": [], "w31": []}
+    with open(os.path.join(GOLDEN, "morton_4x4_ids.txt")) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            t = line.split()
+            if t[0] == "W31":
+                g["w31"].append([int(x) for x in t[1:]])
+            else:
+                g["pairs"].append([int(x) for x in t])
+    a, b, z = (np.array(c, dtype=np.uint64) for c in zip(*g["pairs"]))
+    np.testing.assert_array_equal(oracle.morton_code([a, b], [2, 2]), z)
+    a, b, z = (np.array(c, dtype=np.uint64) for c in zip(*g["w31"]))
+    np.testing.assert_array_equal(oracle.morton_code([a, b], [3, 1]), z)
+
+
+def test_morton_code_single_id_is_the_id():
+    v = np.arange(1000, dtype=np.uint64)
+    np.testing.assert_array_equal(oracle.morton_code([v], [10]), v)
+
+
+@pytest.mark.parametrize("dims,nnz,seed", [((40, 30, 20), 800, 0), ((9, 8, 7, 6), 500, 1)])
+def test_morton_layout_properties(dims, nnz, seed):
+    idx, _ = random_coo(dims, nnz, seed=seed, distinct=False)
+    N = len(dims)
+    m = [3] * N
+    for n in range(N):
+        o = oracle.layout_order_morton(idx, n, m, dims)
+        assert np.array_equal(np.sort(o), np.arange(nnz))
+        ssn = idx[n][o] // m[n]
+        assert np.all(np.diff(ssn.astype(np.int64)) >= 0)     # super-shards of mode n contiguous
+        others = [(n + t) % N for t in range(1, N)]
+        widths = [max(1, ((dims[w] + m[w] - 1) // m[w] - 1).bit_length()) for w in others]
+        code = oracle.morton_code([idx[w][o].astype(np.uint64) // m[w] for w in others], widths).astype(np.int64)
+        same = np.diff(ssn.astype(np.int64)) == 0
+        dc = np.diff(code)
+        assert np.all(dc[same] >= 0)                         # Z order inside a super-shard
+        assert np.all(np.diff(o.astype(np.int64))[same & (dc == 0)] > 0)   # ties in input order
+        # the top bit of every other mode's id is the leading part of the code:
+        # within a super-shard the tuple of top bits never decreases
+        top = np.zeros(nnz, dtype=np.int64)
+        L = max(widths)
+        for w, b in zip(others, widths):
+            if b == L:
+                top = top * 2 + ((idx[w][o] // m[w]) >> (L - 1)).astype(np.int64)
+        assert np.all(np.diff(top)[same] >= 0)
+
+
+def test_morton_layout_with_one_other_mode_varying_is_the_key_order():
+    # when all but one of the other modes have a single super-shard, the Z code
+    # is that mode's id and the Morton layout equals the key order
+    rng = np.random.default_rng(3)
+    dims = (20, 50, 4)
+    idx = np.stack([rng.integers(0, 20, 300), rng.integers(0, 50, 300), rng.integers(0, 4, 300)]).astype(np.uint32)
+    m = [5, 5, 4]
+    np.testing.assert_array_equal(oracle.layout_order_morton(idx, 0, m, dims), oracle.layout_order(idx, 0, m))
