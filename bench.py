@@ -162,9 +162,10 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows), "power_w_max": max(power) if power else None}
 
 
-def cpu_oracle_pass(idx, vals, facs, dims, sample):
+def cpu_oracle_pass(idx, vals, facs, dims, sample, threads=1):
     """The FP64 oracle over the first ``sample`` nonzeros (COO order is random),
-    all modes; returns (seconds, algorithmic bytes of the sample)."""
+    all modes, on ``threads`` host threads; returns (seconds, algorithmic bytes
+    of the sample, nonzeros in the sample)."""
     import oracle
     S = min(sample, idx.shape[1])
     sidx = idx[:, :S].copy()
@@ -172,7 +173,10 @@ def cpu_oracle_pass(idx, vals, facs, dims, sample):
     Y64 = oracle.factors_f64(facs)
     t0 = time.perf_counter()
     for n in range(len(dims)):
-        oracle.mttkrp(sidx, svals, Y64, n, dims)
+        if threads == 1:
+            oracle.mttkrp(sidx, svals, Y64, n, dims)
+        else:
+            oracle.mttkrp_threads(sidx, svals, Y64, n, threads, dims)
     sec = time.perf_counter() - t0
     _, b = step_bytes(dims, S, facs[0].shape[1], 4, 16)
     return sec, b, S
@@ -600,11 +604,18 @@ def main(argv=None):
 
     # ---- CPU baseline: the oracle on a bounded sample (rank 0, single GPU only)
     cpu = None
+    cpu_threads = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         sec, b, S = cpu_oracle_pass(idx, vals, facs, wl.dims, args.cpu_sample)
         cpu = {"value": b / sec / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
                "sample": f"first {S} nonzeros (random COO order) of the workload, all {N} modes, "
                          f"FP64 single-threaded C oracle, {sec:.2f} s"}
+        nthr = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+        if nthr > 1:
+            sec_t, b_t, S_t = cpu_oracle_pass(idx, vals, facs, wl.dims, args.cpu_sample, threads=nthr)
+            cpu_threads = {"value": b_t / sec_t / 1e9, "unit": "GB/s", "cores": nthr, "kind": "oracle",
+                           "sample": f"the same {S_t} nonzeros, FP64 C oracle split over {nthr} threads "
+                                     f"(fixed chunks, private outputs added in thread order), {sec_t:.2f} s"}
 
     # ---- precision: FP32 against BF16 factor storage on the 4-mode 140M-nonzero
     # tensor, all modes, each with its per-mode error against the FP64 oracle
@@ -656,7 +667,7 @@ def main(argv=None):
             "cp_als": als, "cpopt": cpopt, **extra,
             "memory": {"device_bytes": info["device_bytes"], "tensor_bytes": wl.nnz * elem_bytes,
                        "device_over_tensor": info["device_bytes"] / max(1, wl.nnz * elem_bytes)},
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "roofline": roofline, "cpu_baseline": cpu, "cpu_baseline_threads": cpu_threads, "e2e": e2e,
             "gpu_launches": launches_per_step * args.steps, "clocks": clk,
         }
         print(json.dumps(line), flush=True)

@@ -17,6 +17,7 @@
  * given order.  Nothing is blocked, fused or reordered.
  */
 #include <math.h>
+#include <pthread.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -47,6 +48,76 @@ int oracle_mttkrp(int N, const uint64_t *dims, uint64_t nnz, const uint32_t *idx
     }
     free(ell);
     return 0;
+}
+
+/* The same sum split over `threads` POSIX threads for the timed CPU         */
+/* baseline: thread t runs the loop above over the contiguous nonzeros       */
+/* [t*nnz/threads, (t+1)*nnz/threads) into a private FP64 matrix, and the    */
+/* private matrices are added into M in thread order, so the result does not */
+/* depend on thread timing.  threads = 1 is the sequential loop.             */
+struct mt_job {
+    int N, R, n;
+    const uint64_t *dims;
+    uint64_t nnz, lo, hi;
+    const uint32_t *idx;
+    const double *vals;
+    const double *const *Y;
+    double *M;
+    int rc;
+};
+
+static void *mt_run(void *arg)
+{
+    struct mt_job *j = (struct mt_job *)arg;
+    double *ell = (double *)malloc((size_t)j->R * sizeof(double));
+    if (!ell) { j->rc = -2; return NULL; }
+    memset(j->M, 0, (size_t)j->dims[j->n] * (size_t)j->R * sizeof(double));
+    for (uint64_t e = j->lo; e < j->hi; ++e) {
+        for (int r = 0; r < j->R; ++r) ell[r] = 1.0;
+        for (int w = 0; w < j->N; ++w) {
+            if (w == j->n) continue;
+            const double *row = j->Y[w] + (size_t)j->idx[(size_t)w * j->nnz + e] * (size_t)j->R;
+            for (int r = 0; r < j->R; ++r) ell[r] *= row[r];
+        }
+        double *out = j->M + (size_t)j->idx[(size_t)j->n * j->nnz + e] * (size_t)j->R;
+        for (int r = 0; r < j->R; ++r) out[r] += j->vals[e] * ell[r];
+    }
+    free(ell);
+    j->rc = 0;
+    return NULL;
+}
+
+int oracle_mttkrp_threads(int N, const uint64_t *dims, uint64_t nnz, const uint32_t *idx,
+                          const double *vals, const double *const *Y, int R, int n, int threads,
+                          double *M)
+{
+    if (N < 1 || n < 0 || n >= N || R < 1 || threads < 1 || threads > 256) return -1;
+    if (threads == 1) return oracle_mttkrp(N, dims, nnz, idx, vals, Y, R, n, M);
+    const size_t cells = (size_t)dims[n] * (size_t)R;
+    struct mt_job *jobs = (struct mt_job *)calloc((size_t)threads, sizeof(struct mt_job));
+    pthread_t *tid = (pthread_t *)calloc((size_t)threads, sizeof(pthread_t));
+    double *priv = (double *)malloc((size_t)threads * cells * sizeof(double));
+    if (!jobs || !tid || !priv) { free(jobs); free(tid); free(priv); return -2; }
+    int started = 0, rc = 0;
+    for (int t = 0; t < threads; ++t) {
+        jobs[t] = (struct mt_job){N, R, n, dims, nnz, nnz * (uint64_t)t / (uint64_t)threads,
+                                  nnz * (uint64_t)(t + 1) / (uint64_t)threads, idx, vals, Y,
+                                  priv + (size_t)t * cells, -3};
+        if (pthread_create(&tid[t], NULL, mt_run, &jobs[t]) != 0) { rc = -4; break; }
+        ++started;
+    }
+    for (int t = 0; t < started; ++t) pthread_join(tid[t], NULL);
+    for (int t = 0; t < started && rc == 0; ++t)
+        if (jobs[t].rc) rc = jobs[t].rc;
+    if (rc == 0) {
+        memcpy(M, priv, cells * sizeof(double));
+        for (int t = 1; t < threads; ++t) {
+            const double *p = priv + (size_t)t * cells;
+            for (size_t c = 0; c < cells; ++c) M[c] += p[c];
+        }
+    }
+    free(jobs); free(tid); free(priv);
+    return rc;
 }
 
 /* Same sum, restricted to a list of output rows (for full-size sampling).   */

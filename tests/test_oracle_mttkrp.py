@@ -183,3 +183,20 @@ def test_bf16_rounding_agrees_with_torch():
     r = np.random.default_rng(1).standard_normal(50000).astype(np.float32) * 37
     ref = torch.from_numpy(r).to(torch.bfloat16).to(torch.float32).numpy()
     np.testing.assert_array_equal(oracle.round_bf16(r), ref)
+
+
+@pytest.mark.parametrize("threads", [1, 2, 3, 8])
+def test_threaded_oracle_equals_sequential(threads):
+    # the threaded baseline is the same sum split into fixed chunks: bit-equal
+    # with one thread, equal to FP64 rounding otherwise, and repeatable
+    dims = (40, 30, 20)
+    idx, vals = random_coo(dims, 5000, seed=7, law="zipf", distinct=False, value_law="normal")
+    facs = [np.random.default_rng(w).standard_normal((d, 8)) for w, d in enumerate(dims)]
+    for n in range(3):
+        ref = oracle.mttkrp(idx, vals, facs, n, dims)
+        got = oracle.mttkrp_threads(idx, vals, facs, n, threads, dims)
+        if threads == 1:
+            np.testing.assert_array_equal(got, ref)
+        else:
+            np.testing.assert_allclose(got, ref, rtol=1e-12, atol=1e-12)
+        np.testing.assert_array_equal(got, oracle.mttkrp_threads(idx, vals, facs, n, threads, dims))
