@@ -297,6 +297,23 @@ flycoo_status flycoo_cp_als_step(flycoo_handle h, void *const *h_factors, flycoo
                                  double *d_lambda, double *h_fit, flycoo_stream_t stream);
 
 /* ------------------------------------------------------------------------ */
+/* flycoo_cp_als -- `iters` CP-ALS iterations in one call (Algorithm 1's     */
+/* loop), each exactly as flycoo_cp_als_step.  The Gram matrices are        */
+/* computed from the factors as given once, at the start; later iterations  */
+/* reuse the Gram matrix computed after each factor update, which the       */
+/* single-step call cannot (the caller may change the factors between        */
+/* calls).  The results equal `iters` calls of flycoo_cp_als_step.           */
+/*  iters   1 .. 10^6                                                       */
+/*  h_fits  HOST array of `iters` doubles (the fit after each iteration), or */
+/*          NULL                                                            */
+/* Other arguments, allocation and errors as flycoo_cp_als_step; waits for  */
+/* `stream` once, at the end.  After NOT_SPD in some iteration, the later    */
+/* ones leave the factors unchanged.                                        */
+/* ------------------------------------------------------------------------ */
+flycoo_status flycoo_cp_als(flycoo_handle h, void *const *h_factors, flycoo_dtype fdt, int R, int iters,
+                            double *d_lambda, double *h_fits, flycoo_stream_t stream);
+
+/* ------------------------------------------------------------------------ */
 /* flycoo_remap -- dynamic tensor remapping alone (Section III-B): move the  */
 /* tensor from its current layout to L_next_mode.  Each step stores every    */
 /* nonzero at its slot of the following mode's layout; the call takes       */

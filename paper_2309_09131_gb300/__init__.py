@@ -9,6 +9,7 @@ from ._native import (  # noqa: F401
     F32,
     FlycooError,
     flycoo_all_modes_host,
+    flycoo_cp_als,
     flycoo_cp_als_step,
     flycoo_cpopt_grad,
     flycoo_debug_fail_alloc_after,

@@ -70,6 +70,7 @@ def lib():
             "flycoo_mttkrp_adjoint": [P, I, P, I, I, P, P, P, P],
             "flycoo_cpopt_grad": [P, P, I, P, P, P],
             "flycoo_cp_als_step": [P, P, I, I, P, P, P],
+            "flycoo_cp_als": [P, P, I, I, I, P, P, P],
             "flycoo_get_info": [P, P],
             "flycoo_export_layout": [P, P, P, P],
             "flycoo_export_partition": [P, I, P, P, P],
@@ -278,6 +279,23 @@ def flycoo_cp_als_step(h, factors: Sequence[torch.Tensor], lam: torch.Tensor, st
     _check(lib().flycoo_cp_als_step(h, F, BF16 if dt == torch.bfloat16 else F32, int(R), Lp, ctypes.byref(fit),
                                     _stream(stream)))
     return fit.value
+
+
+def flycoo_cp_als(h, factors: Sequence[torch.Tensor], lam: torch.Tensor, iters: int, stream=None) -> List[float]:
+    """``iters`` CP-ALS iterations in one call (the Gram matrices carried from
+    one iteration to the next); returns the fit after each iteration."""
+    R = factors[0].shape[1]
+    dt = factors[0].dtype
+    if dt not in (torch.float32, torch.bfloat16) or any(f.dtype != dt for f in factors):
+        raise TypeError("factors must all be float32 or all bfloat16")
+    F = _ptr_array(factors, (dt,), "factor")
+    Lp = _dev_ptr(lam, (torch.float64,), "lambda")
+    if lam.numel() < R:
+        raise ValueError(f"lambda holds {lam.numel()} values, R = {R}")
+    fits = (ctypes.c_double * int(iters))()
+    _check(lib().flycoo_cp_als(h, F, BF16 if dt == torch.bfloat16 else F32, int(R), int(iters), Lp, fits,
+                               _stream(stream)))
+    return list(fits)
 
 
 def flycoo_debug_set_wait_limit(h, polls: int) -> None:

@@ -491,8 +491,8 @@ void launch_apply(int R, const float *M, const double *W, float2 *Y, u64 I, doub
 
 } // namespace
 
-flycoo_status als_step(Tensor &t, void *const *F, flycoo_dtype fdt, int R, double *d_lambda, double *h_fit,
-                       cudaStream_t s) {
+flycoo_status als_step(Tensor &t, void *const *F, flycoo_dtype fdt, int R, int iters, double *d_lambda,
+                       double *h_fits, cudaStream_t s, const char *who) {
     const int N = t.N;
     const bool bf = fdt == FLYCOO_BF16;
     AlsWork &w = t.als;
@@ -512,6 +512,7 @@ flycoo_status als_step(Tensor &t, void *const *F, flycoo_dtype fdt, int R, doubl
         w.nblk = nblk;
         w.normx2_valid = false;
     }
+    if (w.fits.bytes < (size_t)iters * sizeof(double)) FLY_TRY(w.fits.alloc((size_t)iters * sizeof(double)));
     double *G = w.G.as<double>();
     double *scal = w.scal.as<double>(); // [0] ||X||^2, [1] fit, [2] status word, [4..] partials
     u32 *status = reinterpret_cast<u32 *>(scal + 2);
@@ -536,40 +537,47 @@ flycoo_status als_step(Tensor &t, void *const *F, flycoo_dtype fdt, int R, doubl
         w.normx2_valid = true;
     }
     if (!(w.normx2 > 0.0)) {
-        set_error("flycoo_cp_als_step: the tensor has no nonzero value (||X|| = 0, fit undefined)");
+        set_error("%s: the tensor has no nonzero value (||X|| = 0, fit undefined)", who);
         return FLYCOO_ERR_INVALID_ARG;
     }
     const size_t RR = (size_t)R * R;
+    // the Gram matrices of the factors as given; later iterations of this call
+    // reuse the ones computed after each update
     for (int n = 0; n < N; ++n) FLY_TRY(gram(F[n], bf, t.dims[n], R, G + n * RR, w.gpart.as<double>(), nblk, s));
     FLY_TRY_CUDA(cudaMemsetAsync(status, 0, sizeof(u32), s));
-    for (int n = 0; n < N; ++n) {
-        const u64 I = t.dims[n];
-        FLY_TRY(run_pass(t, n, F, fdt, R, w.M.as<float>(), nullptr, nullptr, s));
-        ldl_inverse_kernel<<<(R + kInvWarps - 1) / kInvWarps, kInvWarps * 32, (RR + R) * sizeof(double), s>>>(
-            G, N, n, R, w.W.as<double>(), status);
-        launch_apply(R, w.M.as<float>(), w.W.as<double>(), w.Y.as<float2>(), I, w.colsq.as<double>(), status, nblk,
-                     s);
-        reduce_partials_kernel<<<(R + 31) / 32, 256, 0, s>>>(w.colsq.as<double>(), nblk, R, d_lambda, 1, status);
-        const bool last = n == N - 1;
-        float *Mlast = last ? w.M.as<float>() : nullptr;
-        double *inner = last ? w.inner.as<double>() : nullptr;
-        launch_normalize(R, bf, w.Y.as<float2>(), d_lambda, F[n], I, Mlast, inner, status, nblk, s);
+    double *fits = w.fits.as<double>();
+    for (int it = 0; it < iters; ++it) {
+        for (int n = 0; n < N; ++n) {
+            const u64 I = t.dims[n];
+            FLY_TRY(run_pass(t, n, F, fdt, R, w.M.as<float>(), nullptr, nullptr, s));
+            ldl_inverse_kernel<<<(R + kInvWarps - 1) / kInvWarps, kInvWarps * 32, (RR + R) * sizeof(double), s>>>(
+                G, N, n, R, w.W.as<double>(), status);
+            launch_apply(R, w.M.as<float>(), w.W.as<double>(), w.Y.as<float2>(), I, w.colsq.as<double>(), status,
+                         nblk, s);
+            reduce_partials_kernel<<<(R + 31) / 32, 256, 0, s>>>(w.colsq.as<double>(), nblk, R, d_lambda, 1, status);
+            const bool last = n == N - 1;
+            float *Mlast = last ? w.M.as<float>() : nullptr;
+            double *inner = last ? w.inner.as<double>() : nullptr;
+            launch_normalize(R, bf, w.Y.as<float2>(), d_lambda, F[n], I, Mlast, inner, status, nblk, s);
+            FLY_TRY_CUDA(cudaGetLastError());
+            FLY_TRY(gram(F[n], bf, I, R, G + n * RR, w.gpart.as<double>(), nblk, s));
+        }
+        fit_kernel<<<1, kAlsThreads, 0, s>>>(G, N, R, d_lambda, w.inner.as<double>(), nblk, scal, fits + it);
         FLY_TRY_CUDA(cudaGetLastError());
-        FLY_TRY(gram(F[n], bf, I, R, G + n * RR, w.gpart.as<double>(), nblk, s));
     }
-    fit_kernel<<<1, kAlsThreads, 0, s>>>(G, N, R, d_lambda, w.inner.as<double>(), nblk, scal, scal + 1);
-    FLY_TRY_CUDA(cudaGetLastError());
     double res[3];
     FLY_TRY_CUDA(cudaMemcpyAsync(res, scal, sizeof(res), cudaMemcpyDeviceToHost, s));
-    FLY_TRY(check_error_word(t, s, "flycoo_cp_als_step"));
+    if (h_fits)
+        FLY_TRY_CUDA(cudaMemcpyAsync(h_fits, fits, (size_t)iters * sizeof(double), cudaMemcpyDeviceToHost, s));
+    FLY_TRY(check_error_word(t, s, who));
     u32 st;
     memcpy(&st, &res[2], sizeof(st));
     if (st) {
-        set_error("flycoo_cp_als_step: a normal-equation matrix (hadamard of Gram matrices) is not positive "
-                  "definite; the modes before it were updated, the others are unchanged");
+        set_error("%s: a normal-equation matrix (hadamard of Gram matrices) is not positive definite; the modes "
+                  "before it were updated, the others are unchanged",
+                  who);
         return FLYCOO_ERR_NOT_SPD;
     }
-    if (h_fit) *h_fit = res[1];
     return FLYCOO_OK;
 }
 

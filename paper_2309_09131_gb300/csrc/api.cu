@@ -758,7 +758,36 @@ extern "C" flycoo_status flycoo_cp_als_step(flycoo_handle h, void *const *h_fact
     DeviceGuard dg(t.device);
     FLY_TRY(dg.status(__func__));
     FLY_TRY(check_usable(t, "flycoo_cp_als_step"));
-    return als_step(t, h_factors, fdt, R, d_lambda, h_fit, reinterpret_cast<cudaStream_t>(stream));
+    return als_step(t, h_factors, fdt, R, 1, d_lambda, h_fit, reinterpret_cast<cudaStream_t>(stream),
+                    "flycoo_cp_als_step");
+}
+
+extern "C" flycoo_status flycoo_cp_als(flycoo_handle h, void *const *h_factors, flycoo_dtype fdt, int R, int iters,
+                                       double *d_lambda, double *h_fits, flycoo_stream_t stream) {
+    clear_error();
+    if (!h) {
+        set_error("flycoo_cp_als: handle is NULL");
+        return FLYCOO_ERR_INVALID_ARG;
+    }
+    Tensor &t = *h;
+    if (fdt != FLYCOO_F32 && fdt != FLYCOO_BF16) {
+        set_error("flycoo_cp_als: unknown factor dtype %d", (int)fdt);
+        return FLYCOO_ERR_INVALID_ARG;
+    }
+    if (iters < 1 || iters > 1000000) {
+        set_error("flycoo_cp_als: iters = %d outside [1, 10^6]", iters);
+        return FLYCOO_ERR_INVALID_ARG;
+    }
+    FLY_TRY(check_factor_ptrs(t, reinterpret_cast<const void *const *>(h_factors), -1, R, "flycoo_cp_als"));
+    if (!d_lambda) {
+        set_error("flycoo_cp_als: d_lambda is NULL");
+        return FLYCOO_ERR_INVALID_ARG;
+    }
+    DeviceGuard dg(t.device);
+    FLY_TRY(dg.status("flycoo_cp_als"));
+    FLY_TRY(check_usable(t, "flycoo_cp_als"));
+    return als_step(t, h_factors, fdt, R, iters, d_lambda, h_fits, reinterpret_cast<cudaStream_t>(stream),
+                    "flycoo_cp_als");
 }
 
 extern "C" flycoo_status flycoo_remap(flycoo_handle h, int next_mode, flycoo_stream_t stream) {

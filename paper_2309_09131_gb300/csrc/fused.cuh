@@ -51,14 +51,17 @@
 
 namespace flycoo {
 
-// row flushes add to shared memory with red.shared.add (1) or with a load,
-// add and store (0)
-#ifndef FLYCOO_FLUSH_RED
-#define FLYCOO_FLUSH_RED 0
-#endif
 // warps whose groups all have full slices skip the clamps and weights (1)
 #ifndef FLYCOO_FULL_FAST
 #define FLYCOO_FULL_FAST 1
+#endif
+// warps of a thread block of the fused kernel
+#ifndef FLYCOO_WARPS
+#define FLYCOO_WARPS 8
+#endif
+// registers of gathered factor data a lane may hold per compute step
+#ifndef FLYCOO_LOAD_REGS
+#define FLYCOO_LOAD_REGS 32
 #endif
 
 // 16-byte loads of one factor row per lane for FP32 factors: a lane takes
@@ -92,7 +95,7 @@ struct FusedCfg {
     static constexpr int VEC = CPL * CV;            // factor values per lane
     static constexpr int L = R / VEC;               // lanes per group
     static constexpr int GPW = 32 / L;              // groups per warp
-    static constexpr int WARPS = 8;
+    static constexpr int WARPS = FLYCOO_WARPS;
     static constexpr int THREADS = WARPS * 32;
     static constexpr int G = WARPS * GPW;           // groups per block
     static constexpr int EW = (N + 1 <= 4) ? 4 : 8; // 32-bit words per stored nonzero
@@ -112,7 +115,7 @@ struct FusedCfg {
     // the larger stage tile when kBlocksPerSM blocks of it fit in an SM's 228 KB
     // (1 KB of each block is reserved by the system); FLYCOO_STAGE_TILE forces one
 #ifdef FLYCOO_STAGE_TILE
-    static constexpr int TZ = FLYCOO_STAGE_TILE == 1024 ? 1 : 0;
+    static constexpr int TZ = FLYCOO_STAGE_TILE == FLYCOO_STAGE_TILE_LARGE ? 1 : 0;
 #else
     static constexpr int TZ = (kBlocksPerSM * (smem_bytes(kStageTile[1]) + 1024) <= 228 * 1024) ? 1 : 0;
 #endif
@@ -283,12 +286,6 @@ __device__ __forceinline__ void st_no_l1(uint4 *p, const uint4 v, uint64_t polic
 #endif
 }
 
-// shared-memory add without a returned value; used where one thread group is
-// the only writer of the row during the tile, so the order of adds is fixed
-__device__ __forceinline__ void red_shared_add(float *p, float v) {
-    asm volatile("red.shared.add.f32 [%0], %1;" ::"r"(smem_addr(p)), "f"(v) : "memory");
-}
-
 template <int VEC>
 __device__ __forceinline__ void store_vec(float *dst, const float *v) {
 #pragma unroll
@@ -320,7 +317,7 @@ __device__ __forceinline__ void add_vec(float *acc, const float *src) {
 constexpr u32 kTileFirst = 1u, kTileLast = 2u, kTileAlone = 4u;
 
 template <int N, int R, bool BF16, bool CPOPT>
-__global__ void __launch_bounds__(256, kBlocksPerSM) fused_mttkrp_remap_kernel(const FusedArgs a) {
+__global__ void __launch_bounds__(FLYCOO_WARPS * 32, kBlocksPerSM) fused_mttkrp_remap_kernel(const FusedArgs a) {
     using C = FusedCfg<N, R, BF16>;
     static_assert(!(CPOPT && BF16), "the CP-OPT gradient pass takes FP32 factors");
     constexpr int VEC = C::VEC;     // factor values per lane
@@ -336,9 +333,10 @@ __global__ void __launch_bounds__(256, kBlocksPerSM) fused_mttkrp_remap_kernel(c
     // nonzeros per group per step: the gathered rows of a step take at most 32
     // registers per lane (U * NF * CPL loads of CW words)
     constexpr int LOADREGS = NF * CPL * C::CW;
-    constexpr int U = (N >= 5 || 32 / LOADREGS < 1)
+    constexpr int U = (N >= 5 || FLYCOO_LOAD_REGS / LOADREGS < 1)
                           ? 1
-                          : ((32 / LOADREGS) > FLYCOO_UNROLL3 ? FLYCOO_UNROLL3 : 32 / LOADREGS);
+                          : ((FLYCOO_LOAD_REGS / LOADREGS) > FLYCOO_UNROLL3 ? FLYCOO_UNROLL3
+                                                                            : FLYCOO_LOAD_REGS / LOADREGS);
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float *acc = reinterpret_cast<float *>(smem_raw + 2 * C::STAGE);          // [M][R]
     float *hacc = acc + M * R;                                               // [G][R] head partials
@@ -372,17 +370,11 @@ __global__ void __launch_bounds__(256, kBlocksPerSM) fused_mttkrp_remap_kernel(c
 #pragma unroll
         for (int c = 0; c < CPL; ++c) add_vec<CV>(v + c * CV, row + c * (R / CPL) + k * CV);
     };
-    // add this lane's values to a row of the accumulator in shared memory
+    // add this lane's values to a row of the accumulator in shared memory (a
+    // load, add and store: measured faster than red.shared.add here)
     auto lane_red = [&](float *row, float *v) {
-#if FLYCOO_FLUSH_RED
-#pragma unroll
-        for (int c = 0; c < CPL; ++c)
-#pragma unroll
-            for (int q = 0; q < CV; ++q) red_shared_add(row + c * (R / CPL) + k * CV + q, v[c * CV + q]);
-#else
         lane_add(v, row);
         lane_store(row, v);
-#endif
     };
     const uint64_t pol_stream = l2_policy_evict_first();
     const uint64_t pol_factor = l2_policy_evict_last();

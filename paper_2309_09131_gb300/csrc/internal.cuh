@@ -159,12 +159,14 @@ struct AlsWork {
     DevBuf colsq;   // per-block column sums of squares
     DevBuf inner;   // per-block partials of <X, Xhat>
     DevBuf scal;    // small FP64 results (||X||^2, fit) and the status word
+    DevBuf fits;    // the fit after each iteration of one call
     u64 rows = 0;
     int nblk = 0;
     bool normx2_valid = false;
     double normx2 = 0.0;
     u64 bytes() const {
-        return M.bytes + Y.bytes + G.bytes + gpart.bytes + W.bytes + colsq.bytes + inner.bytes + scal.bytes;
+        return M.bytes + Y.bytes + G.bytes + gpart.bytes + W.bytes + colsq.bytes + inner.bytes + scal.bytes +
+               fits.bytes;
     }
 };
 
@@ -217,7 +219,14 @@ constexpr u32 kMaxSuperShardRows = 128;
 // of 1024 positions from the shard start when three blocks of that size fit on
 // an SM, else 512) and computes each tile in row order through its
 // precomputed permutation; the schedule and the permutations exist for both sizes
-constexpr u32 kStageTile[2] = {512u, 1024u};
+#ifndef FLYCOO_STAGE_TILE_SMALL
+#define FLYCOO_STAGE_TILE_SMALL 512
+#endif
+#ifndef FLYCOO_STAGE_TILE_LARGE
+#define FLYCOO_STAGE_TILE_LARGE 1024
+#endif
+constexpr u32 kStageTile[2] = {FLYCOO_STAGE_TILE_SMALL, FLYCOO_STAGE_TILE_LARGE};
+static_assert(FLYCOO_STAGE_TILE_LARGE <= 0xffffu && FLYCOO_STAGE_TILE_SMALL % 8 == 0, "stage tile sizes");
 // iteration limit of every device-side wait (mbarrier polls); ~0.1-1 s
 constexpr u32 kSpinLimit = 1u << 24;
 
@@ -308,9 +317,10 @@ flycoo_status run_pass(Tensor &t, int mode, const void *const *F, flycoo_dtype f
 // error word (waits for the stream; TIMEOUT when a bounded wait gave up)
 flycoo_status check_usable(const Tensor &t, const char *who);
 flycoo_status check_error_word(Tensor &t, cudaStream_t s, const char *who);
-// K7/K8: one CP-ALS iteration, modes 0..N-1, from layout L_0 (als.cu)
-flycoo_status als_step(Tensor &t, void *const *F, flycoo_dtype fdt, int R, double *d_lambda, double *h_fit,
-                       cudaStream_t s);
+// K7/K8: `iters` CP-ALS iterations, modes 0..N-1 each, from layout L_0; the
+// fit after each iteration into h_fits (nullable); waits for the stream (als.cu)
+flycoo_status als_step(Tensor &t, void *const *F, flycoo_dtype fdt, int R, int iters, double *d_lambda,
+                       double *h_fits, cudaStream_t s, const char *who);
 flycoo_status launch_fixup(int R, const FixupArgs &a, cudaStream_t s);
 // gradient of spMTTKRP_mode with respect to the nonzero values for the upstream
 // gradient G (I_mode x R, type fdt): d_gvals[e] for every input position e; the

@@ -101,7 +101,12 @@ class FlycooTensor:
 
     def cp_als(self, factors: Sequence[torch.Tensor], iters: int, tol: float = 0.0, stream=None):
         """CP-ALS iterations until ``iters`` are done or the fit changes by
-        less than ``tol``; returns ``(lambda, fits)``."""
+        less than ``tol``; returns ``(lambda, fits)``.  Without a tolerance
+        the iterations run in one library call."""
+        R = factors[0].shape[1]
+        if tol <= 0.0:
+            lam = torch.empty(R, dtype=torch.float64, device=factors[0].device)
+            return lam, nat.flycoo_cp_als(self.h, factors, lam, iters, stream)
         fits: List[float] = []
         lam = None
         for _ in range(iters):

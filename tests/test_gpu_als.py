@@ -337,3 +337,31 @@ def test_als_checkpoint_resume_is_bitwise(P, tmp_path):
     np.testing.assert_array_equal(to_np(lam_c), to_np(lam_a))
     for a, c in zip(Ya, Yc):
         np.testing.assert_array_equal(to_np(a), to_np(c))
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16])
+def test_multi_iteration_call_equals_single_steps(P, dtype):
+    # flycoo_cp_als carries the Gram matrices between its iterations; the
+    # factors, lambda and fits are bit for bit those of repeated single steps
+    dims = (200, 150, 100)
+    idx, vals = random_coo(dims, 25_000, seed=18, law="zipf", value_law="int1to5")
+    facs = make_factors(dims, 32, "normal_over_sqrt_r", seed=18)
+    Ta = P.FlycooTensor(idx, vals, dims, g=600, bins=29)
+    Ya = [torch.from_numpy(f).cuda().to(dtype).contiguous() for f in facs]
+    lam_a = torch.empty(32, dtype=torch.float64, device="cuda")
+    fits_a = P.flycoo_cp_als(Ta.h, Ya, lam_a, 6)
+    Tb = P.FlycooTensor(idx, vals, dims, g=600, bins=29)
+    Yb = [torch.from_numpy(f).cuda().to(dtype).contiguous() for f in facs]
+    fits_b = []
+    lam_b = None
+    for _ in range(6):
+        lam_b, fit = Tb.cp_als_step(Yb, lam_b)
+        fits_b.append(fit)
+    assert fits_a == fits_b
+    assert torch.equal(lam_a, lam_b)
+    for a, b in zip(Ya, Yb):
+        assert torch.equal(a, b)
+    assert Ta.layout_mode == 0
+    with pytest.raises(P.FlycooError) as e:
+        P.flycoo_cp_als(Ta.h, Ya, lam_a, 0)
+    assert e.value.status_name == "FLYCOO_ERR_INVALID_ARG"
