@@ -43,12 +43,14 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
 
 def test_profiled_traffic_is_plausible_for_the_current_kernel():
     # the bench's roofline "traffic" comes from the committed ncu summary only
-    # when it was captured on this exact kernel source; then it must sit at or
-    # above the algorithmic bytes of a 77M-nonzero pass and within 2x of them
+    # when it was captured on this exact kernel source; then it must sit near
+    # the algorithmic bytes of a 77M-nonzero pass: at most 2x, and at least 0.9x
+    # (a pass ends with part of its remap writes still in L2; they reach DRAM
+    # during the next launch, so one launch's counters can read a little low)
     import bench
     t = bench.traffic_from_profiles(bench.kernel_source_sha())
     if t is None:
         pytest.skip("the committed ncu summary predates the current kernel source")
     per_mode, _ = bench.step_bytes((12000, 9000, 29000), 77_000_000, 32, 4, 16)
     alg = sum(per_mode) / 3
-    assert alg <= t <= 2 * alg, (t, alg)
+    assert 0.9 * alg <= t <= 2 * alg, (t, alg)
