@@ -47,6 +47,7 @@ def parse_args(argv=None):
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
     ap.add_argument("--g", type=int, default=0, help="shard size (0: the library default)")
     ap.add_argument("--bins", type=int, default=0, help="schedule bins (0: the library default)")
+    ap.add_argument("--m", type=int, default=0, help="super-shard width of every mode (0: the library default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-bf16", action="store_true")
     ap.add_argument("--no-als", action="store_true")
@@ -310,11 +311,11 @@ def run_reference(args):
     return 0
 
 
-def traffic_from_profiles(kernel_sha):
+def traffic_from_profiles(kernel_sha, g):
     """DRAM bytes per 77M-nonzero launch of the fused kernel from the
-    committed ncu summary, if it was taken on this exact kernel source; else
-    None."""
-    p = os.path.join(ROOT, "profiles", "fused_mttkrp_remap_f32_nell2like_16m_g16384.md")
+    committed ncu summary at shard size g, if it was taken on this exact kernel
+    source; else None."""
+    p = os.path.join(ROOT, "profiles", f"fused_mttkrp_remap_f32_nell2like_16m_g{int(g)}.md")
     try:
         kv = {}
         with open(p) as f:
@@ -374,7 +375,8 @@ def main(argv=None):
 
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    T = P.FlycooTensor(idx, vals, wl.dims, g=args.g, bins=args.bins)
+    T = P.FlycooTensor(idx, vals, wl.dims, g=args.g, bins=args.bins,
+                       m=[min(args.m, d) for d in wl.dims] if args.m else None)
     torch.cuda.synchronize()
     create_s = time.perf_counter() - t0
     info = T.info
@@ -422,7 +424,7 @@ def main(argv=None):
     sha = kernel_source_sha()
     # the committed capture (a 16M-nonzero case of the same shape at the bench's
     # shard size, scaled to 77M nonzeros) describes the bench workload only
-    traffic = traffic_from_profiles(sha) if wl.name == DEFAULT_WORKLOAD else None
+    traffic = traffic_from_profiles(sha, T.info["g"]) if wl.name == DEFAULT_WORKLOAD else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak if achieved else None, "traffic": traffic,
                 "peak_kind": peak_kind, "kernel": f"fused_mttkrp_remap_kernel<{N},{R},fp32>",
@@ -528,7 +530,7 @@ def main(argv=None):
         T.remap(0)
         extra["no_remap_ms_per_mode"] = nr
         ranks = {}
-        for R2 in (16, 32, 64):
+        for R2 in (16, 32, 64) + ((128,) if N == 3 else ()):
             Y2 = [torch.from_numpy(f).cuda() for f in make_factors(wl.dims, R2, wl.factor_law, seed=wl.seed)]
             o2 = [torch.empty((d, R2), dtype=torch.float32, device="cuda") for d in wl.dims]
             for _ in range(2):
@@ -544,18 +546,15 @@ def main(argv=None):
             ranks[str(R2)] = s0.elapsed_time(s1) / args.steps
             del Y2, o2
         extra["all_mode_ms_by_rank_fp32"] = ranks
-        # rank 128 needs super-shards of at most 64 rows: a handle with m = 64,
-        # timed at R = 64 and R = 128 for the comparison
-        T64 = P.FlycooTensor(idx, vals, wl.dims, m=[min(64, d) for d in wl.dims]) if N == 3 else None
-        if T64 is not None:
-            r64 = {}
-            for R2 in (64, 128):
-                Y2 = [torch.from_numpy(f).cuda() for f in make_factors(wl.dims, R2, wl.factor_law, seed=wl.seed)]
-                o2 = [torch.empty((d, R2), dtype=torch.float32, device="cuda") for d in wl.dims]
-                r64[str(R2)] = time_all_modes(P, T64, Y2, o2, args.steps)[0]
-                del Y2, o2
-            extra["all_mode_ms_by_rank_fp32_m64"] = r64
-            T64.close()
+        # super-shard width m_n (Section III-A): the default min(I_n, 32) against
+        # 16 and 64 rows, FP32 at the workload's rank
+        widths = {}
+        for mw in (16, 64):
+            Tm = P.FlycooTensor(idx, vals, wl.dims, m=[min(mw, d) for d in wl.dims])
+            widths[str(mw)] = time_all_modes(P, Tm, Yf, outs, args.steps)[0]
+            Tm.close()
+        widths[str(32)] = time_all_modes(P, T, Yf, outs, args.steps)[0]
+        extra["all_mode_ms_by_super_shard_rows_fp32"] = widths
         # the same sweep with the block-cyclic schedule instead of Algorithm 3 (LPT)
         Tb = P.FlycooTensor(idx, vals, wl.dims, schedule=P._native.SCHEDULE_BLOCK_CYCLIC)
         for _ in range(2):

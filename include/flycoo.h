@@ -54,13 +54,14 @@ typedef enum {
 
 /* Partitioning parameters (Section III-A and III-C).  Zero selects the default.
  *  m[n]  super-shard width of mode n: super-shard j holds the nonzeros whose
- *        mode-n index lies in [j*m[n], (j+1)*m[n]).  At most 128: the fused
+ *        mode-n index lies in [j*m[n], (j+1)*m[n]).  At most 64: the fused
  *        kernel keeps a super-shard's m[n] output rows in shared memory (the
- *        cache budget of Eq. 3).  Default min(I_n, 128).
+ *        cache budget of Eq. 3).  Default min(I_n, 32): fewer rows per stage
+ *        tile give longer row runs and more factor-row cache hits.
  *  g     shard size in nonzeros: each super-shard is cut into runs of g
  *        consecutive nonzeros (the last one shorter).  Default: the largest
- *        power of two in [1024, 32768] that leaves at least eight shards per
- *        bin (1024 when none does).
+ *        power of two in [1024, 32768] that leaves at least sixteen shards
+ *        per bin (1024 when none does).
  *  bins  number of schedule bins of Algorithm 3, which is also the number of
  *        thread blocks of the fused kernel; at most 2^20.  Default: 3 x the
  *        SM count.
@@ -132,7 +133,7 @@ typedef struct flycoo_tensor *flycoo_handle;
 /*  out     receives the handle.                                             */
 /* With params->order = FLYCOO_ORDER_MORTON the order inside each           */
 /* super-shard is the Z-Morton variant described at flycoo_params.           */
-/* Errors: INVALID_ARG (also m[n] > 128, bins > 2^20, unknown schedule or    */
+/* Errors: INVALID_ARG (also m[n] > 64, bins > 2^20, unknown schedule or     */
 /* order, Morton codes wider than 64 bits),                                  */
 /* INDEX_RANGE (any coordinate >= its I_w), UNSUPPORTED (N outside 3..5,     */
 /* nnz >= 2^32 - 1), OOM, CUDA.  Waits for `stream`.                         */
@@ -155,10 +156,8 @@ void flycoo_destroy(flycoo_handle h);
 /*  h_factors  HOST array of N DEVICE pointers, Y_w is I_w x R row-major in  */
 /*             `fdt`, 16-byte aligned.  Entry `mode` is not read (may be     */
 /*             NULL).                                                        */
-/*  R          rank: 16, 32 or 64; or 128 on a 3-mode tensor whose mode     */
-/*             `mode` has super-shards of at most 64 rows (flycoo_params.m:  */
-/*             the m x R FP32 accumulator lives in shared memory), else      */
-/*             UNSUPPORTED.                                                  */
+/*  R          rank: 16, 32 or 64; or 128 on a 3-mode tensor (else          */
+/*             UNSUPPORTED).                                                 */
 /*  d_out      I_mode x R FP32, 16-byte aligned, written in full.  It must   */
 /*             not overlap a factor.                                         */
 /*  next_mode  -1: no remap.  (mode + 1) mod N: store every nonzero at its   */
@@ -179,8 +178,7 @@ flycoo_status flycoo_spmttkrp(flycoo_handle h, int mode, const void *const *h_fa
 /* its pass ends; then wait for the stream and check the device error word. */
 /*  h_factors  HOST array of N HOST pointers, Y_w is I_w x R row-major in   */
 /*             `fdt` (pinned memory makes the copies asynchronous)          */
-/*  R          16, 32 or 64, or 128 as flycoo_spmttkrp allows it (every    */
-/*             mode then needs m <= 64)                                     */
+/*  R          16, 32 or 64, or 128 as flycoo_spmttkrp allows it            */
 /*  h_out      HOST array of N HOST pointers, M_n is I_n x R FP32,          */
 /*             overwritten                                                  */
 /* The first call allocates device staging for the factors and outputs     */

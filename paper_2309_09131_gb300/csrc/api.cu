@@ -162,9 +162,12 @@ flycoo_status check_error_word(Tensor &t, cudaStream_t s, const char *who) {
 // per bin: fewer, larger shards leave the last whole shard in a bin dominating
 // its load (on a 77M-nonzero 3-mode tensor four per bin put 16% more nonzeros
 // in the heaviest bin than the mean), many smaller ones add row-block flushes
+// the largest power of two up to 32768 that gives every bin at least 16 shards
+// (whole 1024-nonzero stage tiles from 1024 up): finer shards balance the bins
+// and keep each super-shard's segments short, at the price of more row blocks
 u64 default_shard_size(u64 nnz, u32 bins) {
     u64 g = 32768;
-    while (g > 1024 && nnz / g < 8ull * bins) g >>= 1;
+    while (g > 1024 && nnz / g < 16ull * bins) g >>= 1;
     return g;
 }
 
@@ -257,6 +260,12 @@ void plan_mode(ModePlan &md, u64 nnz, u64 g, u32 bins, u32 schedule) {
     md.k4_items.clear();
     for (u64 j = 0; j < md.k; ++j)
         if (md.ss_seg_ptr[j + 1] - md.ss_seg_ptr[j] != 1) md.k4_items.push_back((u32)j);
+    md.k4_order.clear();
+    for (u32 j : md.k4_items)
+        if (md.ss_seg_ptr[j + 1] - md.ss_seg_ptr[j] <= kFixupLightSegs) md.k4_order.push_back(j);
+    md.k4_nlight = (u32)md.k4_order.size();
+    for (u32 j : md.k4_items)
+        if (md.ss_seg_ptr[j + 1] - md.ss_seg_ptr[j] > kFixupLightSegs) md.k4_order.push_back(j);
 }
 
 flycoo_status partition_mode(Tensor &t, int n, const std::vector<u32> &ssp, cudaStream_t s) {
@@ -267,7 +276,7 @@ flycoo_status partition_mode(Tensor &t, int n, const std::vector<u32> &ssp, cuda
     md.ss_ptr.assign(ssp.begin(), ssp.end());
     plan_mode(md, t.nnz, t.g, t.bins, t.schedule);
     FLY_TRY(upload(md.d_ss_seg_ptr, md.ss_seg_ptr, s));
-    FLY_TRY(upload(md.d_k4, md.k4_items, s));
+    FLY_TRY(upload(md.d_k4, md.k4_order, s));
     for (int z = 0; z < 2; ++z) {
         FLY_TRY(upload(md.d_tiles[z], md.tiles[z], s));
         FLY_TRY(upload(md.d_tile_bin_ptr[z], md.tile_bin_ptr[z], s));
@@ -277,8 +286,9 @@ flycoo_status partition_mode(Tensor &t, int n, const std::vector<u32> &ssp, cuda
 
 flycoo_status launch_fixup(int R, const FixupArgs &a, cudaStream_t s) {
     if (a.nitems == 0) return FLYCOO_OK;
-    const u32 rows = std::min<u32>(a.m, a.I_out);
-    const dim3 grid(a.nitems, (rows * (u32)R + 63) / 64);
+    // one block per light item, one per 64 floats of a row block per other item
+    const u32 chunks = (a.m * (u32)R + 63) / 64;
+    const u32 grid = a.nlight + (a.nitems - a.nlight) * chunks;
     super_shard_fixup_kernel<<<grid, 256, 0, s>>>(a, (u32)R);
     FLY_TRY_CUDA(cudaGetLastError());
     return FLYCOO_OK;
@@ -310,7 +320,8 @@ FixupArgs fixup_args(const Tensor &t, int mode, float *d_out, const float *parti
     const ModeMeta &md = t.mode[mode];
     FixupArgs f{};
     f.items = md.d_k4.as<u32>();
-    f.nitems = (u32)md.k4_items.size();
+    f.nitems = (u32)md.k4_order.size();
+    f.nlight = md.k4_nlight;
     f.ss_seg_ptr = md.d_ss_seg_ptr.as<u32>();
     f.partials = partials;
     f.out = d_out;
@@ -395,7 +406,7 @@ static flycoo_status create_impl(int N, const uint64_t *h_dims, uint64_t nnz, co
     }
     for (int w = 0; w < N; ++w) {
         // a super-shard's output rows live in shared memory: at most kMaxSuperShardRows
-        u64 m = (params && params->m[w]) ? params->m[w] : std::min<u64>(h_dims[w], kMaxSuperShardRows);
+        u64 m = (params && params->m[w]) ? params->m[w] : std::min<u64>(h_dims[w], kDefaultSuperShardRows);
         if (m > kMaxSuperShardRows) {
             set_error("flycoo_create: m[%d] = %llu exceeds %u rows", w, (unsigned long long)m, kMaxSuperShardRows);
             return FLYCOO_ERR_INVALID_ARG;

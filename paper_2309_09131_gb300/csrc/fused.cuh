@@ -707,30 +707,67 @@ __global__ void __launch_bounds__(FLYCOO_WARPS * 32, kBlocksPerSM) fused_mttkrp_
 }
 
 // K4: rows of the super-shards that do not have exactly one segment: the sum of
-// their segments' row blocks in schedule order (zero for an empty
-// super-shard).  Block (item, c) covers 64 consecutive floats of the
-// super-shard's rows; its four 64-thread parts take every fourth block and are
-// added in part order.
+// their segments' row blocks (zero for an empty super-shard), in an order fixed
+// by the plan, so the sum is the same in every run.
+//  * A light item (at most kFixupLightSegs segments) has one block: thread t
+//    sums float4 columns t, t + 256, ... of the row blocks in four interleaved
+//    chains (segments i, i + 4, i + 8, ... in chain i), added as (0 + 1) + (2 + 3).
+//  * Any other item has one block per 64 floats of its row block: 16 parts of 16
+//    threads take every 16th segment, each part in four chains the same way,
+//    and the parts are added in a fixed tree order.
+// Independent chains keep four loads of a thread in flight, and a light item's
+// dependent loads (item, segment range, row blocks) are paid once per block.
 static __global__ void __launch_bounds__(256) super_shard_fixup_kernel(const FixupArgs a, u32 R) {
-    __shared__ float part_sum[4][64];
-    const u32 item = blockIdx.x;
+    constexpr u32 kParts = 16, kChains = 4;
+    __shared__ float4 part_sum[kParts][16];
+    const u32 b = blockIdx.x;
+    const bool light = b < a.nlight;
+    const u32 chunks = (a.m * R + 63) / 64;
+    const u32 item = light ? b : a.nlight + (b - a.nlight) / chunks;
     const u32 j = a.items[item];
     const u32 row_base = j * a.m;
     const u32 m_eff = min(a.m, a.I_out - row_base);
-    const u32 nfl = m_eff * R;
-    const u32 f = blockIdx.y * 64 + (threadIdx.x & 63);
-    const u32 part = threadIdx.x >> 6;
+    const u32 nfl = m_eff * R;                         // a multiple of 4 (R is)
     const u32 s0 = a.ss_seg_ptr[j], s1 = a.ss_seg_ptr[j + 1];
-    float sum = 0.f;
-    if (f < nfl)
-        for (u32 s = s0 + part; s < s1; s += 4) sum += a.partials[(size_t)s * a.m * R + f];
-    part_sum[part][threadIdx.x & 63] = sum;
-    __syncthreads();
-    if (threadIdx.x < 64 && f < nfl) {
-        const float t = ((part_sum[0][threadIdx.x] + part_sum[1][threadIdx.x]) + part_sum[2][threadIdx.x]) +
-                        part_sum[3][threadIdx.x];
-        a.out[(size_t)row_base * R + f] = t;
+    const size_t block = (size_t)a.m * R;
+    auto add4 = [](float4 p, float4 q) { return make_float4(p.x + q.x, p.y + q.y, p.z + q.z, p.w + q.w); };
+    // chains c of segments first, first + stride c, first + 2 stride c, ... below s1
+    auto chains = [&](u32 first, u32 stride, u32 f) {
+        float4 ch[kChains];
+#pragma unroll
+        for (u32 c = 0; c < kChains; ++c) ch[c] = make_float4(0.f, 0.f, 0.f, 0.f);
+        u32 s = first;
+        for (; s + (kChains - 1) * stride < s1; s += kChains * stride) {
+            float4 x[kChains];
+#pragma unroll
+            for (u32 c = 0; c < kChains; ++c)
+                x[c] = *reinterpret_cast<const float4 *>(a.partials + (size_t)(s + c * stride) * block + f);
+#pragma unroll
+            for (u32 c = 0; c < kChains; ++c) ch[c] = add4(ch[c], x[c]);
+        }
+        // at most kChains - 1 segments are left
+#pragma unroll
+        for (u32 c = 0; c + 1 < kChains; ++c)
+            if (s + c * stride < s1)
+                ch[c] = add4(ch[c], *reinterpret_cast<const float4 *>(a.partials + (size_t)(s + c * stride) * block + f));
+        return add4(add4(ch[0], ch[1]), add4(ch[2], ch[3]));
+    };
+    if (light) {
+        for (u32 f = threadIdx.x * 4; f < nfl; f += 256 * 4)
+            *reinterpret_cast<float4 *>(a.out + (size_t)row_base * R + f) = chains(s0, 1, f);
+        return;
     }
+    const u32 c4 = threadIdx.x & 15;
+    const u32 part = threadIdx.x >> 4;
+    const u32 f = (b - a.nlight) % chunks * 64 + c4 * 4;
+    part_sum[part][c4] = f < nfl ? chains(s0 + part, kParts, f) : make_float4(0.f, 0.f, 0.f, 0.f);
+    __syncthreads();
+#pragma unroll
+    for (u32 h = kParts / 2; h >= 1; h >>= 1) {
+        if (part < h) part_sum[part][c4] = add4(part_sum[part][c4], part_sum[part + h][c4]);
+        __syncthreads();
+    }
+    if (part == 0 && f < nfl) *reinterpret_cast<float4 *>(a.out + (size_t)row_base * R + f) = part_sum[0][c4];
 }
 
 template <int N, int R, bool BF16, bool CPOPT = false>

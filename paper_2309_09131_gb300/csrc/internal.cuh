@@ -130,6 +130,10 @@ struct ModePlan {
     std::vector<u32> seg_ss;                // segments: super-shard of each
     std::vector<u32> ss_seg_ptr;            // k + 1
     std::vector<u32> k4_items;              // super-shards whose rows K4 writes (not exactly one segment)
+    // K4's launch order of k4_items: the k4_nlight items of at most
+    // kFixupLightSegs segments first, then the others
+    std::vector<u32> k4_order;
+    u32 k4_nlight = 0;
     std::vector<u32> tile_ptr[2];           // T_z + 1: stage tiles of each size (K1 only)
     // tile descriptors in block-schedule order (bin b: tiles [tile_bin_ptr[b],
     // tile_bin_ptr[b+1])), four words each: start, len | flags << 16,
@@ -214,7 +218,18 @@ constexpr int kRank128 = 128;
 constexpr u32 kMaxRowsAtRank128 = 64;
 // largest super-shard width m_n: the fused kernel keeps a super-shard's output
 // rows (m_n x R FP32) in shared memory
-constexpr u32 kMaxSuperShardRows = 128;
+#ifndef FLYCOO_MAX_SS_ROWS
+#define FLYCOO_MAX_SS_ROWS 64
+#endif
+constexpr u32 kMaxSuperShardRows = FLYCOO_MAX_SS_ROWS;
+static_assert(kMaxSuperShardRows >= 32 && kMaxSuperShardRows % 32 == 0 && kMaxSuperShardRows <= 1024,
+              "super-shard rows: a multiple of 32");
+// default super-shard width: min(I_n, 32).  Narrower super-shards put fewer
+// output rows in a stage tile (longer row runs, fewer accumulator flushes) and
+// fewer factor rows behind each key window (more L1 hits); measured on a
+// 77M-nonzero 3-mode tensor: 32 rows 3.71 ms all-mode, 64 rows 3.78, 16 rows
+// 3.94, 128 rows 4.49
+constexpr u32 kDefaultSuperShardRows = 32;
 // stage tiles: the fused kernel streams a shard one stage tile at a time (runs
 // of 1024 positions from the shard start when three blocks of that size fit on
 // an SM, else 512) and computes each tile in row order through its
@@ -293,9 +308,13 @@ struct FusedArgs {
     u32 wait_limit;            // polls of a tile's barrier before the pass gives up
 };
 
+// K4 gives a super-shard of at most this many segments one thread block
+constexpr u32 kFixupLightSegs = 16;
+
 struct FixupArgs {
-    const u32 *items;          // super-shards K4 writes
+    const u32 *items;          // super-shards K4 writes: nlight light ones, then the others
     u32 nitems;
+    u32 nlight;
     const u32 *ss_seg_ptr;     // row blocks of super-shard j: [ss_seg_ptr[j], ss_seg_ptr[j+1])
     const float *partials;
     float *out;

@@ -362,11 +362,15 @@ __global__ void __launch_bounds__(256)
         __syncwarp();
     }
     __syncthreads();
+    // warp 0 turns the counts into start offsets: lane l owns the PER rows
+    // l*PER .. l*PER + PER-1, warps in order inside a row
+    constexpr int PER = M / 32;
+    static_assert(M >= 32 && M % 32 == 0, "the row scan gives each lane M / 32 rows");
     if (warp == 0) {
-        u32 tot[4], run = 0;
-        for (int c = 0; c < 4; ++c) {
+        u32 tot[PER], run = 0;
+        for (int c = 0; c < PER; ++c) {
             u32 t = 0;
-            for (int w = 0; w < W; ++w) t += cnt[w][lane * 4 + c];
+            for (int w = 0; w < W; ++w) t += cnt[w][lane * PER + c];
             tot[c] = t;
             run += t;
         }
@@ -376,11 +380,11 @@ __global__ void __launch_bounds__(256)
             if (lane >= d) incl += y;
         }
         u32 base = incl - run;
-        for (int c = 0; c < 4; ++c) {
+        for (int c = 0; c < PER; ++c) {
             u32 o = base;
             for (int w = 0; w < W; ++w) {
-                const u32 x = cnt[w][lane * 4 + c];
-                cnt[w][lane * 4 + c] = o;
+                const u32 x = cnt[w][lane * PER + c];
+                cnt[w][lane * PER + c] = o;
                 o += x;
             }
             base += tot[c];

@@ -48,7 +48,8 @@ def test_profiled_traffic_is_plausible_for_the_current_kernel():
     # (a pass ends with part of its remap writes still in L2; they reach DRAM
     # during the next launch, so one launch's counters can read a little low)
     import bench
-    t = bench.traffic_from_profiles(bench.kernel_source_sha())
+    # the bench tensor's default shard size: 77M nonzeros over 3 x 152 bins
+    t = bench.traffic_from_profiles(bench.kernel_source_sha(), 8192)
     if t is None:
         pytest.skip("the committed ncu summary predates the current kernel source")
     per_mode, _ = bench.step_bytes((12000, 9000, 29000), 77_000_000, 32, 4, 16)

@@ -42,7 +42,7 @@ LAYOUT_CASES = [
     ((4, 3, 3, 2, 2), 100, 2, "uniform", False, (2, 1, 1, 1, 1), 5, 4),
     ((50, 2, 3), 150, 3, "zipf", True, (7, 1, 1), 1, 2),
     ((1000, 800, 600), 20000, 4, "zipf", True, (0, 0, 0), 0, 0),
-    ((300, 200, 250), 30000, 6, "zipf", True, (128, 5, 1), 777, 13),
+    ((300, 200, 250), 30000, 6, "zipf", True, (64, 5, 1), 777, 13),
     ((3, 1, 700), 700, 5, "uniform", True, (1, 1, 10), 64, 9),
 ]
 
@@ -339,16 +339,22 @@ def test_rank128_all_modes(P, dims, nnz, law, m, g, bins):
             assert rel_fro(to_np(outs[n]), ref) <= FP32_TOL, (dtype, n, rel_fro(to_np(outs[n]), ref))
 
 
-def test_rank128_needs_narrow_super_shards_and_three_modes(P):
+def test_super_shard_width_limit_and_rank128_modes(P):
+    # the accumulator holds at most 64 rows of a super-shard: wider m is
+    # rejected at creation; rank 128 is built for 3-mode tensors only
     dims = (300, 200, 100)
     idx, vals = random_coo(dims, 5_000, seed=13)
-    facs = [torch.randn((d, 128), device="cuda") for d in dims]
-    out = torch.empty((300, 128), device="cuda")
-    T = P.FlycooTensor(idx, vals, dims)          # default m = 128
     with pytest.raises(P.FlycooError) as e:
-        P.flycoo_spmttkrp(T.h, 0, facs, out, 1)
-    assert e.value.status_name == "FLYCOO_ERR_UNSUPPORTED" and "m[0] <= 64" in str(e.value)
-    assert T.layout_mode == 0
+        P.FlycooTensor(idx, vals, dims, m=(65, 32, 32))
+    assert e.value.status_name == "FLYCOO_ERR_INVALID_ARG" and "exceeds 64 rows" in str(e.value)
+    T = P.FlycooTensor(idx, vals, dims)          # default m = min(I_n, 32)
+    assert T.info["m"] == [32, 32, 32]
+    facs = [torch.randn((d, 128), device="cuda") for d in dims]
+    outs = T.all_modes(facs)
+    torch.cuda.synchronize()
+    Y64 = [to_np(f).astype(np.float64) for f in facs]
+    for n in range(3):
+        assert rel_fro(to_np(outs[n]), oracle.mttkrp(idx, vals, Y64, n, dims)) <= FP32_TOL, n
     dims4 = (30, 20, 10, 8)
     idx4, vals4 = random_coo(dims4, 2_000, seed=14)
     T4 = P.FlycooTensor(idx4, vals4, dims4, m=(16, 16, 8, 8))
@@ -356,8 +362,9 @@ def test_rank128_needs_narrow_super_shards_and_three_modes(P):
     with pytest.raises(P.FlycooError) as e:
         P.flycoo_spmttkrp(T4.h, 0, f4, torch.empty((30, 128), device="cuda"), 1)
     assert e.value.status_name == "FLYCOO_ERR_UNSUPPORTED" and "3-mode" in str(e.value)
+    assert T4.layout_mode == 0
     # the handle stays usable at a built rank
-    T.all_modes([f[:, :64].contiguous() for f in facs])
+    T4.all_modes([f[:, :64].contiguous() for f in f4])
     torch.cuda.synchronize()
 
 

@@ -154,8 +154,8 @@ def test_block_cyclic(P):
                                       (77_000_000, 456), (3_000_000, 17)])
 def test_default_shard_size(P, nnz, bins):
     g = int(_plan(P, nnz, [0, nnz], 0, bins)["g"][0])
-    # the largest power of two in [1024, 32768] leaving at least eight shards per bin
-    cands = [1 << e for e in range(10, 16) if (1 << e) == 1024 or nnz // (1 << e) >= 8 * bins]
+    # the largest power of two in [1024, 32768] leaving at least sixteen shards per bin
+    cands = [1 << e for e in range(10, 16) if (1 << e) == 1024 or nnz // (1 << e) >= 16 * bins]
     assert g == max(cands)
 
 

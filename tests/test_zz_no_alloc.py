@@ -52,16 +52,16 @@ def test_static_scratch_matches_allocated_scratch(P, dims, nnz, R, dtype, g):
 
 
 def test_static_scratch_at_its_size_limit(P):
-    # one 128-row super-shard per mode, 256 equal shards and 256 bins: each bin
-    # holds one shard, so every mode has 256 segments, and at R = 64 their row
-    # blocks fill the 8 MiB array exactly (256 x 128 x 64 x 4 bytes)
-    dims = (128, 128, 128)
+    # one 64-row super-shard per mode, 512 equal shards and 512 bins: each bin
+    # holds one shard, so every mode has 512 segments, and at R = 64 their row
+    # blocks fill the 8 MiB array exactly (512 x 64 x 64 x 4 bytes)
+    dims = (64, 64, 64)
     R = 64
-    idx, vals = random_coo(dims, 256 * 64, seed=22, law="uniform", distinct=False, value_law="normal")
+    idx, vals = random_coo(dims, 512 * 64, seed=22, law="uniform", distinct=False, value_law="normal")
     facs = [torch.from_numpy(f).cuda() for f in make_factors(dims, R, "normal", seed=22)]
-    T = P.FlycooTensor(idx, vals, dims, g=64, bins=256)
+    T = P.FlycooTensor(idx, vals, dims, m=dims, g=64, bins=512)
     info = T.info
-    assert info["segments"] == [256, 256, 256] and info["m"] == [128, 128, 128]
+    assert info["segments"] == [512, 512, 512] and info["m"] == [64, 64, 64]
     ref = [r.clone() for r in T.all_modes(facs)]
     for call in range(2):
         outs = [torch.full((d, R), float("nan"), device="cuda") for d in dims]
@@ -70,11 +70,11 @@ def test_static_scratch_at_its_size_limit(P):
         torch.cuda.synchronize()
         for n in range(3):
             assert torch.equal(outs[n], ref[n]), (call, n)
-    # one segment more than fits: 257 bins, 257 shards
-    idx, vals = random_coo(dims, 257 * 64, seed=23, law="uniform", distinct=False, value_law="normal")
-    T2 = P.FlycooTensor(idx, vals, dims, g=64, bins=257)
-    assert T2.info["segments"][0] == 257
-    out = torch.empty((128, R), device="cuda")
+    # one segment more than fits: 513 bins, 513 shards
+    idx, vals = random_coo(dims, 513 * 64, seed=23, law="uniform", distinct=False, value_law="normal")
+    T2 = P.FlycooTensor(idx, vals, dims, m=dims, g=64, bins=513)
+    assert T2.info["segments"][0] == 513
+    out = torch.empty((64, R), device="cuda")
     with pytest.raises(P.FlycooError) as e:
         P.flycoo_spmttkrp_static_scratch(T2.h, 0, facs, out, 1)
     assert e.value.status_name == "FLYCOO_ERR_INVALID_ARG"
@@ -82,12 +82,12 @@ def test_static_scratch_at_its_size_limit(P):
 
 
 def test_static_scratch_rejects_oversized_requests(P):
-    # mode 0 has 300 super-shards of 128 rows, each split over several bins:
-    # over 256 row blocks of 128 x 64 floats, more than the 8 MiB array holds
+    # mode 0 has 600 super-shards of 64 rows, each split over several bins:
+    # over 512 row blocks of 64 x 64 floats, more than the 8 MiB array holds
     dims = (38_400, 40, 30)
     idx, vals = random_coo(dims, 20_000, seed=3)
-    T = P.FlycooTensor(idx, vals, dims, g=16, bins=8)
-    assert T.info["segments"][0] > 256
+    T = P.FlycooTensor(idx, vals, dims, m=(64, 40, 30), g=16, bins=8)
+    assert T.info["segments"][0] > 512
     facs = [torch.randn((d, 64), device="cuda") for d in dims]
     out = torch.empty((dims[0], 64), device="cuda")
     with pytest.raises(P.FlycooError) as e:
