@@ -55,6 +55,11 @@ namespace flycoo {
 #ifndef FLYCOO_FULL_FAST
 #define FLYCOO_FULL_FAST 1
 #endif
+// unroll factor of a full tile's compute steps
+#ifndef FLYCOO_FULL_UNROLL
+#define FLYCOO_FULL_UNROLL 2
+#endif
+constexpr int kFullUnroll = FLYCOO_FULL_UNROLL;
 // warps of a thread block of the fused kernel
 #ifndef FLYCOO_WARPS
 #define FLYCOO_WARPS 8
@@ -604,7 +609,13 @@ __global__ void __launch_bounds__(FLYCOO_WARPS * 32, kBlocksPerSM) fused_mttkrp_
             u32 j0 = 0;
             // warp-uniform: every group of the warp has a full slice of whole steps
             if (FLYCOO_FULL_FAST && __all_sync(0xffffffffu, hi - lo == wlen && wlen % U == 0)) {
-                for (; j0 < wlen; j0 += U) steps(j0, Many{}, Yes{});
+                if (kChunkFull % U == 0 && tlen == (u32)CAP) {
+                    // a full tile: every slice is kChunkFull positions, a compile-time trip count
+#pragma unroll kFullUnroll
+                    for (u32 jj = 0; jj < kChunkFull; jj += U) steps(jj, Many{}, Yes{});
+                } else {
+                    for (; j0 < wlen; j0 += U) steps(j0, Many{}, Yes{});
+                }
             } else {
                 for (; j0 + U <= wlen; j0 += U) steps(j0, Many{}, No{});
                 for (; j0 < wlen; ++j0) steps(j0, One{}, No{});
