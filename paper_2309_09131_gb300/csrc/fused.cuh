@@ -16,16 +16,17 @@
 // them in cache, Eq. 3), across all shards of that super-shard that follow
 // each other in the bin (a segment).  One thread streams the tiles with 1-D
 // TMA bulk copies into a two-stage shared buffer on mbarriers, two tiles
-// ahead: the nonzeros, their slots in L_{n+1} and the tile's compute order (a
-// precomputed u16 permutation that sorts the tile stably by output index).
-// It publishes each tile's 16-byte descriptor with it.  For each tile:
+// ahead: the nonzeros and the tile's compute order (a precomputed u16
+// permutation that sorts the tile stably by output index); it prefetches the
+// nonzeros' slots in L_{n+1} into L2 and publishes each tile's 16-byte
+// descriptor with it.  For each tile:
 //
 //  1. remap: every thread stores a few of the tile's nonzeros at their slots of
 //     L_{n+1} (the Store of Algorithm 2's remap step), in one burst, in
 //     layout order;
 //  2. compute: each group of L lanes takes a fixed slice of the tile in its
 //     compute order, where a row's nonzeros are contiguous; its lanes split
-//     the rank dimension (16 bytes of a factor row per lane).  Per nonzero it
+//     the rank dimension (16 or 32 bytes of a factor row per lane).  Per nonzero it
 //     gathers the N-1 input factor rows and adds val * Hadamard product (FP32)
 //     to a running row sum in registers.  A run of one row that lies inside
 //     the slice is added to its shared-memory accumulator by the group alone;
@@ -35,8 +36,8 @@
 //
 // At the end of a segment the accumulator rows go straight to the output when
 // the super-shard has no other segment, else to the segment's row block, and
-// the accumulator is zeroed; K4 then sums the blocks of a super-shard in
-// schedule order.  Every accumulator row is updated by one thread group at a
+// the accumulator is zeroed; K4 then sums the blocks of a super-shard in a
+// fixed order.  Every accumulator row is updated by one thread group at a
 // time, in an order fixed by the layout and the launch shape, so results are
 // bitwise reproducible; no atomics touch the data.  Rows without nonzeros come
 // out as zeros.

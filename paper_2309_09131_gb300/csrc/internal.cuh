@@ -226,9 +226,8 @@ static_assert(kMaxSuperShardRows >= 32 && kMaxSuperShardRows % 32 == 0 && kMaxSu
               "super-shard rows: a multiple of 32");
 // default super-shard width: min(I_n, 32).  Narrower super-shards put fewer
 // output rows in a stage tile (longer row runs, fewer accumulator flushes) and
-// fewer factor rows behind each key window (more L1 hits); measured on a
-// 77M-nonzero 3-mode tensor: 32 rows 3.71 ms all-mode, 64 rows 3.78, 16 rows
-// 3.94, 128 rows 4.49
+// fewer factor rows behind each key window (more L1 hits); on a 77M-nonzero
+// 3-mode tensor at R = 32, 32 rows were faster than 16, 24, 40, 48, 64 or 128
 constexpr u32 kDefaultSuperShardRows = 32;
 // stage tiles: the fused kernel streams a shard one stage tile at a time (runs
 // of 1024 positions from the shard start when three blocks of that size fit on
