@@ -331,12 +331,18 @@ def traffic_from_profiles(kernel_sha, g):
 
 
 def kernel_source_sha():
+    """SHA-256 of the fused kernel's sources with comments and blank space
+    removed, so that a comment edit keeps a capture valid."""
     import hashlib
+    import re
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2309_09131_gb300", "csrc")
     for f in ("fused.cuh", "internal.cuh"):
-        with open(os.path.join(csrc, f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(csrc, f)) as fh:
+            text = fh.read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        h.update("\n".join(" ".join(line.split()) for line in text.splitlines() if line.strip()).encode())
     return h.hexdigest()
 
 

@@ -56,8 +56,10 @@ typedef enum {
  *  m[n]  super-shard width of mode n: super-shard j holds the nonzeros whose
  *        mode-n index lies in [j*m[n], (j+1)*m[n]).  At most 64: the fused
  *        kernel keeps a super-shard's m[n] output rows in shared memory (the
- *        cache budget of Eq. 3).  Default min(I_n, 32): fewer rows per stage
- *        tile give longer row runs and more factor-row cache hits.
+ *        cache budget of Eq. 3).  Default min(I_n, 32) when the dims sum to
+ *        at most 2^18 rows (factor matrices that stay in L2: fewer rows per
+ *        stage tile give longer row runs and more factor-row cache hits),
+ *        else min(I_n, 64).
  *  g     shard size in nonzeros: each super-shard is cut into runs of g
  *        consecutive nonzeros (the last one shorter).  Default: the largest
  *        power of two in [1024, 32768] that leaves at least sixteen shards

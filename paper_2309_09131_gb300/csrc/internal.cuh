@@ -224,10 +224,11 @@ constexpr u32 kMaxRowsAtRank128 = 64;
 constexpr u32 kMaxSuperShardRows = FLYCOO_MAX_SS_ROWS;
 static_assert(kMaxSuperShardRows >= 32 && kMaxSuperShardRows % 32 == 0 && kMaxSuperShardRows <= 1024,
               "super-shard rows: a multiple of 32");
-// default super-shard width: min(I_n, 32).  Narrower super-shards put fewer
+// default super-shard width of tensors with few rows in all modes (factor
+// matrices that stay in L2): min(I_n, 32).  Narrower super-shards put fewer
 // output rows in a stage tile (longer row runs, fewer accumulator flushes) and
-// fewer factor rows behind each key window (more L1 hits); on a 77M-nonzero
-// 3-mode tensor at R = 32, 32 rows were faster than 16, 24, 40, 48, 64 or 128
+// fewer factor rows behind each key window (more L1 hits).  The rule for
+// larger tensors sits beside the shard-size rule of the planner.
 constexpr u32 kDefaultSuperShardRows = 32;
 // stage tiles: the fused kernel streams a shard one stage tile at a time (runs
 // of 1024 positions from the shard start when three blocks of that size fit on

@@ -368,6 +368,24 @@ def test_super_shard_width_limit_and_rank128_modes(P):
     torch.cuda.synchronize()
 
 
+@pytest.mark.parametrize("R", [16, 32, 64])
+def test_all_modes_widest_super_shards(P, R):
+    # 64-row super-shards fill the kernel's accumulator (the default width of
+    # tensors with many rows); FP32 and BF16 factors against the FP64 oracle
+    dims = (3000, 2000, 1000)
+    idx, vals = random_coo(dims, 200_000, seed=41, law="zipf", distinct=True, value_law="lognormal")
+    facs = make_factors(dims, R, "normal", seed=41)
+    T = P.FlycooTensor(idx, vals, dims, m=(64, 64, 64), g=2048, bins=61)
+    assert T.info["m"] == [64, 64, 64]
+    for dtype, bf in ((torch.float32, False), (torch.bfloat16, True)):
+        outs = T.all_modes(_cuda_factors(facs, dtype))
+        torch.cuda.synchronize()
+        Y64 = oracle.factors_f64(facs, bf16=bf)
+        for n in range(3):
+            ref = oracle.mttkrp(idx, vals, Y64, n, dims)
+            assert rel_fro(to_np(outs[n]), ref) <= FP32_TOL, (R, dtype, n, rel_fro(to_np(outs[n]), ref))
+
+
 @pytest.mark.parametrize("case", MTTKRP_CASES[1:5], ids=lambda c: f"{c[0]}-{c[1]}-R{c[3]}")
 def test_all_modes_morton_order(P, case):
     # the Z-Morton variant changes the order inside super-shards, never the result
