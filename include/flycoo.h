@@ -433,7 +433,12 @@ typedef enum {
     FLYCOO_PLAN_TILE_BIN_PTR_1024 = 11, /* bins + 1                           */
     FLYCOO_PLAN_TILES_1024 = 12,        /* 4 x T_1                            */
     FLYCOO_PLAN_SEG_SS = 13,            /* Q: super-shard of each segment     */
-    FLYCOO_PLAN_SS_SEG_PTR = 14         /* k + 1: segments of each super-shard */
+    FLYCOO_PLAN_SS_SEG_PTR = 14,        /* k + 1: segments of each super-shard */
+    /* the fixup kernel's launch order of the K4 items: those of at most 16   */
+    /* segments (one thread block each) in ascending order, then the others   */
+    /* (one block per 64 floats of their row block) in ascending order        */
+    FLYCOO_PLAN_K4_ORDER = 15,          /* |K4 items|                         */
+    FLYCOO_PLAN_K4_NLIGHT = 16          /* 1: how many of them come first     */
 } flycoo_plan_array;
 
 /* Copy array `which` into h_out, widened to uint64.  *count is in: the     */

@@ -38,6 +38,8 @@ from ._native import (  # noqa: F401
 from ._native import (  # noqa: F401
     PLAN_G,
     PLAN_K4_ITEMS,
+    PLAN_K4_NLIGHT,
+    PLAN_K4_ORDER,
     PLAN_SHARD_BIN_PTR,
     PLAN_SHARD_ITEMS,
     PLAN_SHARD_PTR,

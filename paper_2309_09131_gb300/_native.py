@@ -422,6 +422,8 @@ PLAN_TILE_BIN_PTR_1024 = 11
 PLAN_TILES_1024 = 12
 PLAN_SEG_SS = 13
 PLAN_SS_SEG_PTR = 14
+PLAN_K4_ORDER = 15
+PLAN_K4_NLIGHT = 16
 
 
 def flycoo_plan_create(nnz: int, ss_ptr, g: int = 0, bins: int = 1, schedule: int = SCHEDULE_LPT):

@@ -1054,11 +1054,13 @@ extern "C" flycoo_status flycoo_plan_get(flycoo_plan p, int which, uint64_t *h_o
         return FLYCOO_ERR_INVALID_ARG;
     }
     const u64 g1[1] = {p->g};
+    const u64 nl1[1] = {p->k4_nlight};
     const u64 *wide = nullptr;
     const std::vector<u32> *v = nullptr;
     u64 n = 0;
     switch (which) {
     case FLYCOO_PLAN_G: wide = g1; n = 1; break;
+    case FLYCOO_PLAN_K4_NLIGHT: wide = nl1; n = 1; break;
     case FLYCOO_PLAN_SHARD_PTR: v = &p->shard_ptr; break;
     case FLYCOO_PLAN_SHARD_SS: v = &p->shard_ss; break;
     case FLYCOO_PLAN_SS_SHARD_PTR: v = &p->ss_shard_ptr; break;
@@ -1073,6 +1075,7 @@ extern "C" flycoo_status flycoo_plan_get(flycoo_plan p, int which, uint64_t *h_o
     case FLYCOO_PLAN_TILES_1024: v = &p->tiles[1]; break;
     case FLYCOO_PLAN_SEG_SS: v = &p->seg_ss; break;
     case FLYCOO_PLAN_SS_SEG_PTR: v = &p->ss_seg_ptr; break;
+    case FLYCOO_PLAN_K4_ORDER: v = &p->k4_order; break;
     default:
         set_error("flycoo_plan_get: unknown array %d", which);
         return FLYCOO_ERR_INVALID_ARG;

@@ -101,6 +101,13 @@ def _check_against_oracle(P, rows, I, m, g, bins):
     assert np.array_equal(got["seg_ss"], seg_ss)
     assert np.array_equal(got["ss_seg_ptr"], ss_seg_ptr)
     assert np.array_equal(got["k4_items"], np.nonzero(np.diff(ss_seg_ptr) != 1)[0])
+    # the fixup kernel's launch order: super-shards of at most 16 segments (one
+    # block each) first, then the others, each group in ascending order
+    k4 = np.nonzero(np.diff(ss_seg_ptr) != 1)[0]
+    nseg = np.diff(ss_seg_ptr)[k4]
+    light, heavy = k4[nseg <= 16], k4[nseg > 16]
+    assert got["k4_nlight"].tolist() == [light.size]
+    assert np.array_equal(got["k4_order"], np.concatenate([light, heavy]))
     # every shard of a super-shard lies in one of its segments: at most as many
     # segments as shards, and a super-shard with shards has at least one
     assert np.all(np.diff(ss_seg_ptr) <= ss_shards) and np.all((np.diff(ss_seg_ptr) > 0) == (ss_shards > 0))
@@ -229,3 +236,16 @@ def test_plan_get_errors(P):
     finally:
         P.flycoo_plan_destroy(h)
     P.flycoo_plan_destroy(None)
+
+
+def test_fixup_order_light_then_heavy(P):
+    # super-shard 0 spread over 40 bins (40 segments: heavy), super-shard 1 over
+    # a few (light), super-shard 2 in one segment (no fixup), super-shard 3 empty
+    ss_ptr = np.array([0, 40 * 64, 40 * 64 + 3 * 64, 40 * 64 + 3 * 64 + 10, 40 * 64 + 3 * 64 + 10],
+                      dtype=np.uint64)
+    got = _plan(P, int(ss_ptr[-1]), ss_ptr, 64, 40)
+    nseg = np.diff(got["ss_seg_ptr"].astype(np.int64))
+    assert nseg[0] > 16 and 1 < nseg[1] <= 16 and nseg[2] == 1 and nseg[3] == 0
+    assert got["k4_items"].tolist() == [0, 1, 3]
+    assert got["k4_nlight"].tolist() == [2]
+    assert got["k4_order"].tolist() == [1, 3, 0]
